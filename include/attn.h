@@ -1,0 +1,231 @@
+/*
+ * attn.h -- C ABI of the GB300 aTTN ground-state-search library (libattn.so).
+ *
+ * The library implements the hot path of the augmented tree tensor network
+ * (aTTN) ground-state search of "The Augmented Tree Tensor Network Cookbook"
+ * (Reinic, Pavesic, Jaschke, Montangero, arXiv:2507.21236):
+ *   - effective Hamiltonian H_eff of one binary-TTN tensor as a sum over
+ *     tensor-product-operator (TPO) terms (Sec. 3.3.2, Fig. eff-op) and its
+ *     application to the order-3 tensor inside Lanczos (Sec. 4.4.2,
+ *     Fig. eff-op-cost);
+ *   - renormalisation T^T (O (x) O) T of link operators (Fig. eff-op);
+ *   - Lanczos local eigensolver, QR re-isometrisation (Sec. 3.1, Fig. iso);
+ *   - disentangler placement (Sec. 6.1), the mapping H' = D^T H D
+ *     (Sec. 4.3, Algorithm 1) and the MERA-like update (Sec. 4.1.1);
+ *   - the sweep schedule (Sec. 4).
+ * Every compute step runs in the library's own CUDA kernels for sm_103a on
+ * one GPU. There is no CPU fallback: without a usable GPU every compute call
+ * returns ATTN_ECUDA.
+ *
+ * Conventions (all entry points):
+ *  - Status: every call returns attn_status; ATTN_OK == 0. On failure a
+ *    thread-local message is available from attn_last_error(). No C++
+ *    exception crosses this boundary.
+ *  - Streams: a context owns one CUDA stream (given at creation, or its own).
+ *    Device work is enqueued on it. Calls that return host scalars
+ *    (eigenvalues, energies) or copy to host synchronise that stream only.
+ *  - Ownership: handles (attn_ctx, attn_model, attn_state, attn_heff) are
+ *    created and destroyed by the library; all device memory they hold is
+ *    allocated with cudaMalloc and freed by the matching destroy call.
+ *    Pointers passed in (x_dev, y_dev, host arrays) stay owned by the caller
+ *    and are never freed or retained after the call returns.
+ *  - Layout: a node tensor is a C-contiguous FP64 array T[m0][m1][m2] with
+ *    slot 0 = left child link, slot 1 = right child link, slot 2 = parent
+ *    link (the top link for the two top tensors). Link operators are
+ *    row-major FP64 m x m matrices O[out][in] acting on a link index.
+ *  - Sites are numbered along the Hilbert curve (Sec. 6); a node of layer l
+ *    covers 2^l consecutive sites.
+ */
+#ifndef ATTN_H
+#define ATTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ATTN_API __attribute__((visibility("default")))
+
+typedef enum {
+  ATTN_OK = 0,
+  ATTN_EINVAL = 1,         /* bad argument, shape or state (message says which) */
+  ATTN_ENOMEM = 2,         /* device or host allocation failed */
+  ATTN_ECUDA = 3,          /* CUDA runtime error, or no usable GPU */
+  ATTN_ENONFINITE = 4,     /* NaN/Inf found in an input or a result */
+  ATTN_ENOTISOMETRIC = 5,  /* a tensor that must be an isometry is not */
+  ATTN_ENOTCONVERGED = 6,  /* an iteration stopped before its tolerance; best result kept */
+  ATTN_ETIMEOUT = 7,       /* a bounded device-side wait gave up */
+  ATTN_EUNSUPPORTED = 8    /* shape/dtype combination not implemented */
+} attn_status;
+
+typedef enum {
+  ATTN_F64 = 0,  /* FP64 CUDA-core contractions */
+  ATTN_F32 = 1,  /* reserved */
+  ATTN_TF32 = 2, /* reserved */
+  ATTN_BF16 = 3  /* BF16 operands, FP32 accumulation on the tcgen05 tensor cores */
+} attn_dtype;
+
+typedef struct attn_ctx attn_ctx;
+typedef struct attn_model attn_model;
+typedef struct attn_state attn_state;
+typedef struct attn_heff attn_heff;
+
+/* Run parameters. attn_config_default fills the paper's/our defaults. */
+typedef struct {
+  int lanczos_depth;        /* Krylov depth of the local eigensolver (20) */
+  double lanczos_tol;       /* stop when beta_k |y_k| < tol |theta| (1e-13) */
+  int de_max_iter;          /* MERA-like update iterations, Sec. 4.1.1 (20) */
+  double de_rel_dev;        /* relative energy change that stops them (1e-12) */
+  int s_ttn;                /* sweeps without disentangler optimisation, Sec. 6.3 (1) */
+  attn_dtype matvec_dtype;  /* precision of the H_eff contractions in Lanczos (ATTN_F64) */
+  int refine_steps;         /* FP64 residual-correction steps after a low-precision Lanczos (3) */
+  double refine_tol;        /* stop refining when ||H v - theta v|| < tol |theta| (1e-10) */
+  int reserved[8];
+} attn_config;
+
+ATTN_API attn_status attn_config_default(attn_config* cfg);
+
+/* Last error message of the calling thread ("" if none). Valid until the next call. */
+ATTN_API const char* attn_last_error(void);
+
+/* Library version string. */
+ATTN_API const char* attn_version(void);
+
+/* ----------------------------------------------------------------- context */
+
+/* Create a context on the current CUDA device. cuda_stream is a cudaStream_t
+ * (NULL: the library creates its own non-blocking stream). cfg may be NULL
+ * (defaults). */
+ATTN_API attn_status attn_create(const attn_config* cfg, void* cuda_stream, attn_ctx** out);
+ATTN_API attn_status attn_destroy(attn_ctx* ctx);
+ATTN_API attn_status attn_set_config(attn_ctx* ctx, const attn_config* cfg);
+ATTN_API attn_status attn_get_config(attn_ctx* ctx, attn_config* cfg);
+/* Block until all work enqueued by the context has finished. */
+ATTN_API attn_status attn_sync(attn_ctx* ctx);
+/* Number of library kernels launched by this context so far. */
+ATTN_API attn_status attn_kernel_launches(attn_ctx* ctx, uint64_t* count);
+
+/* ------------------------------------------------------------------ models */
+
+/* L x L open square lattice, H = -sum_<ij> Z_i Z_j - h sum_i X_i
+ * (Sec. 6, Eq. qising, in the coupling-on-Z form; same spectrum). L a power of two. */
+ATTN_API attn_status attn_model_tfim(attn_ctx* ctx, int L, double h, attn_model** out);
+/* L x L open triangular lattice (square plus (+1,+1) bonds),
+ * H = J sum_<ij> (Sx Sx + Sy Sy + Sz Sz) with S = sigma/2 (Sec. 6, Eq. xxz);
+ * three separate terms per bond. */
+ATTN_API attn_status attn_model_tri_heisenberg(attn_ctx* ctx, int L, double J, attn_model** out);
+/* Generic Hamiltonian on n_sites spin-1/2 sites (n_sites a power of two >= 4):
+ * term t acts on term_nsites[t] in {1,2,3} ascending sites
+ * term_sites[3t .. 3t+nsites-1] with the real operator
+ * term_ops[64t ...] stored row-major as a (2^k x 2^k) matrix, first site most
+ * significant. One-site terms on the same site are summed (Sec. 3.3).
+ * n_bonds/bond_sites list the candidate disentangler pairs (NULL: the
+ * two-site terms). */
+ATTN_API attn_status attn_model_terms(attn_ctx* ctx, int n_sites, int n_terms, const int* term_nsites,
+                                      const int* term_sites, const double* term_ops, attn_model** out);
+ATTN_API attn_status attn_model_destroy(attn_model* model);
+ATTN_API attn_status attn_model_info(const attn_model* model, int* n_sites, int* n_terms);
+
+/* ------------------------------------------------------------------- state */
+
+/* Build a TTN with bond dimension m for the model's sites (Sec. 3.1): nodes
+ * numbered layer by layer from the bottom, tensors [c0][c1][parent] with link
+ * above a layer-l node of dimension min(2^(2^l), m). raw_host[n] points to
+ * the raw FP64 entries of node n (shape from attn_node_shape, C order); each
+ * non-centre tensor is replaced by the Q factor of its (c0 c1) x parent QR
+ * (R's diagonal >= 0) and the centre (left top node) is normalised -- on the
+ * GPU. Disentanglers start empty (none placed). */
+ATTN_API attn_status attn_state_create(attn_ctx* ctx, const attn_model* model, int m,
+                                       const double* const* raw_host, attn_state** out);
+ATTN_API attn_status attn_state_destroy(attn_state* st);
+/* n_nodes, centre node, number of layers nL. Any pointer may be NULL. */
+ATTN_API attn_status attn_state_info(attn_state* st, int* n_nodes, int* centre, int* n_layers);
+ATTN_API attn_status attn_node_shape(attn_state* st, int node, int shape[3]);
+/* Neighbour of (node, slot): *kind = 0 site (index in *idx), 1 node (*idx, *back slot there). */
+ATTN_API attn_status attn_node_neighbour(attn_state* st, int node, int slot, int* kind, int* idx, int* back);
+/* Copy node tensor to/from host (synchronous). Setting a tensor invalidates
+ * the effective operators that depend on it. */
+ATTN_API attn_status attn_node_get(attn_state* st, int node, double* host_out);
+ATTN_API attn_status attn_node_set(attn_state* st, int node, const double* host_in);
+/* Device pointer of a node tensor (valid until the node changes shape/state is destroyed). */
+ATTN_API attn_status attn_node_device_ptr(attn_state* st, int node, double** dev_ptr);
+/* Move the isometry centre along the tree path with one QR per link (Fig. iso). */
+ATTN_API attn_status attn_move_centre(attn_state* st, int node);
+/* max ||T^T T - 1|| over non-centre tensors (towards the centre). */
+ATTN_API attn_status attn_isometry_error(attn_state* st, double* err);
+
+/* ------------------------------------------------------------ disentanglers */
+
+/* Greedy placement of Sec. 6.1.2 under the restrictions of Sec. 6.1.1, up to
+ * max_de pairs; *n_placed receives the number actually placed. Replaces any
+ * previous placement; all disentanglers start as the identity (Sec. 6). */
+ATTN_API attn_status attn_de_place(attn_state* st, int max_de, int* n_placed);
+/* Sites (i < j) of every placed disentangler, 2 ints each. */
+ATTN_API attn_status attn_de_sites(attn_state* st, int* pairs_out);
+/* Set / get the 4x4 orthogonal matrix u_k (row-major, site i most significant). */
+ATTN_API attn_status attn_de_set(attn_state* st, int k, const double* u16);
+ATTN_API attn_status attn_de_get(attn_state* st, int k, double* u16);
+/* Map the Hamiltonian through the disentangler layer, H' = D^T H D
+ * (Sec. 4.3, Algorithm 1), split the mapped terms into rank-1 products and
+ * rebuild all effective operators towards the current centre (Sec. 3.3.2). */
+ATTN_API attn_status attn_map_hamiltonian(attn_state* st);
+/* Number of mapped terms and rank-1 products of the current H'. */
+ATTN_API attn_status attn_hamiltonian_info(attn_state* st, int* n_terms, int* n_products);
+
+/* -------------------------------------------------------------------- H_eff */
+
+/* Explicit description of a node's effective Hamiltonian (the summed-link
+ * form of Sec. 3.3.2): with x[a][b][c] of shape (m[0], m[1], m[2]),
+ *   y = sum_l H_l x_l x                                  (h_int[l], may be NULL)
+ *     + sum_{k} sum_r (A_r on slot p_k)(B_r on slot q_k) x   (pair kinds k:
+ *                                     0 = slots (0,1), 1 = (0,2), 2 = (1,2))
+ *     + sum_r (O0_r (x) O1_r (x) O2_r) x                 (three-link products).
+ * All operator arrays are DEVICE FP64, row-major; pair_a[k] is [n_pair[k]][m_p][m_p],
+ * pair_b[k] is [n_pair[k]][m_q][m_q], triple[l] is [n_triple][m_l][m_l]. The
+ * library copies them at creation (the caller may free them afterwards). */
+typedef struct {
+  int m[3];
+  const double* h_int[3];
+  int n_pair[3];
+  const double* pair_a[3];
+  const double* pair_b[3];
+  int n_triple;
+  const double* triple[3];
+} attn_heff_desc;
+
+ATTN_API attn_status attn_heff_create(attn_ctx* ctx, const attn_heff_desc* desc, attn_heff** out);
+/* H_eff of `node` built from the state's effective operators (Sec. 3.3.2):
+ * the isometry centre must be at `node` (ATTN_EINVAL otherwise). */
+ATTN_API attn_status attn_heff_build(attn_state* st, int node, attn_heff** out);
+ATTN_API attn_status attn_heff_destroy(attn_heff* h);
+/* Counts: n_pair[3], n_triple, and the algorithmic FLOPs of one apply. */
+ATTN_API attn_status attn_heff_info(attn_heff* h, int n_pair[3], int* n_triple, double* flops);
+/* y_dev = H_eff x_dev (both DEVICE FP64 [m0][m1][m2], distinct buffers),
+ * contractions in `dtype` (ATTN_F64 or ATTN_BF16 with FP32 accumulation).
+ * Asynchronous on the context stream. */
+ATTN_API attn_status attn_heff_apply(attn_heff* h, const double* x_dev, double* y_dev, attn_dtype dtype);
+/* Same with host buffers: copies x in, applies, copies y out (synchronous). */
+ATTN_API attn_status attn_heff_apply_host(attn_heff* h, const double* x_host, double* y_host, attn_dtype dtype);
+
+/* Lowest eigenpair of H_eff by Lanczos (Sec. 4.4.2) started from T_dev
+ * (device [m0][m1][m2]); on return T_dev holds the unit-norm Ritz vector and
+ * *theta the Ritz value. Matvecs in the context's matvec_dtype; when that is
+ * not FP64, refine_steps FP64 residual corrections follow. *iters may be NULL. */
+ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, int* iters);
+
+/* ----------------------------------------------------------- sweep drivers */
+
+/* Local optimisation at `node`: move the centre there, build H_eff, Lanczos,
+ * write the tensor back if the Ritz value does not exceed the current energy. */
+ATTN_API attn_status attn_local_step(attn_state* st, int node, double* energy);
+/* One TTN sweep under the current H' (post-order, Sec. 4 step 3). */
+ATTN_API attn_status attn_ttn_sweep(attn_state* st, double* energy);
+/* Energy <T|H_eff|T> at the centre (FP64). */
+ATTN_API attn_status attn_energy(attn_state* st, double* energy);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ATTN_H */

@@ -1,0 +1,395 @@
+"""Thin ctypes binding of libattn (include/attn.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+computation of its own: arrays are passed as pointers (numpy for host
+buffers; torch CUDA tensors or integer addresses for device buffers), handles
+are opaque ``ctypes.c_void_p`` values, and a non-zero status raises
+``AttnError`` with the library's message. The library has no CPU fallback:
+if ``libattn.so`` is missing this module raises on import of the library.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+ATTN_F64, ATTN_F32, ATTN_TF32, ATTN_BF16 = 0, 1, 2, 3
+STATUS = {0: "ATTN_OK", 1: "ATTN_EINVAL", 2: "ATTN_ENOMEM", 3: "ATTN_ECUDA", 4: "ATTN_ENONFINITE",
+          5: "ATTN_ENOTISOMETRIC", 6: "ATTN_ENOTCONVERGED", 7: "ATTN_ETIMEOUT", 8: "ATTN_EUNSUPPORTED"}
+
+
+class AttnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class attn_config(ctypes.Structure):
+    _fields_ = [("lanczos_depth", ctypes.c_int), ("lanczos_tol", ctypes.c_double),
+                ("de_max_iter", ctypes.c_int), ("de_rel_dev", ctypes.c_double),
+                ("s_ttn", ctypes.c_int), ("matvec_dtype", ctypes.c_int),
+                ("refine_steps", ctypes.c_int), ("refine_tol", ctypes.c_double),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class attn_heff_desc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int * 3), ("h_int", ctypes.c_void_p * 3), ("n_pair", ctypes.c_int * 3),
+                ("pair_a", ctypes.c_void_p * 3), ("pair_b", ctypes.c_void_p * 3),
+                ("n_triple", ctypes.c_int), ("triple", ctypes.c_void_p * 3)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_PI = ctypes.POINTER(ctypes.c_int)
+_PD = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "attn_config_default": [ctypes.POINTER(attn_config)],
+    "attn_create": [ctypes.POINTER(attn_config), _P, _PP],
+    "attn_destroy": [_P],
+    "attn_set_config": [_P, ctypes.POINTER(attn_config)],
+    "attn_get_config": [_P, ctypes.POINTER(attn_config)],
+    "attn_sync": [_P],
+    "attn_kernel_launches": [_P, ctypes.POINTER(ctypes.c_uint64)],
+    "attn_model_tfim": [_P, _I, _D, _PP],
+    "attn_model_tri_heisenberg": [_P, _I, _D, _PP],
+    "attn_model_terms": [_P, _I, _I, _PI, _PI, _PD, _PP],
+    "attn_model_destroy": [_P],
+    "attn_model_info": [_P, _PI, _PI],
+    "attn_state_create": [_P, _P, _I, ctypes.POINTER(_PD), _PP],
+    "attn_state_destroy": [_P],
+    "attn_state_info": [_P, _PI, _PI, _PI],
+    "attn_node_shape": [_P, _I, _PI],
+    "attn_node_neighbour": [_P, _I, _I, _PI, _PI, _PI],
+    "attn_node_get": [_P, _I, _PD],
+    "attn_node_set": [_P, _I, _PD],
+    "attn_node_device_ptr": [_P, _I, ctypes.POINTER(_P)],
+    "attn_move_centre": [_P, _I],
+    "attn_isometry_error": [_P, _PD],
+    "attn_de_place": [_P, _I, _PI],
+    "attn_de_sites": [_P, _PI],
+    "attn_de_set": [_P, _I, _PD],
+    "attn_de_get": [_P, _I, _PD],
+    "attn_map_hamiltonian": [_P],
+    "attn_hamiltonian_info": [_P, _PI, _PI],
+    "attn_heff_create": [_P, ctypes.POINTER(attn_heff_desc), _PP],
+    "attn_heff_build": [_P, _I, _PP],
+    "attn_heff_destroy": [_P],
+    "attn_heff_info": [_P, _PI, _PI, _PD],
+    "attn_heff_apply": [_P, _P, _P, _I],
+    "attn_heff_apply_host": [_P, _PD, _PD, _I],
+    "attn_eigsolve": [_P, _P, _PD, _PI],
+    "attn_local_step": [_P, _I, _PD],
+    "attn_ttn_sweep": [_P, _PD],
+    "attn_energy": [_P, _PD],
+}
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(path=None):
+    """Load libattn.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with `python -m paper_2507_21236_gb300._build` "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.attn_last_error.restype = ctypes.c_char_p
+    lib.attn_last_error.argtypes = []
+    lib.attn_version.restype = ctypes.c_char_p
+    lib.attn_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS) + ["attn_last_error", "attn_version"]
+
+
+def _check(st):
+    if st != 0:
+        raise AttnError(st, load().attn_last_error().decode())
+
+
+def _ptr(a):
+    """Device address of a torch tensor / int, or None."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    return a.data_ptr()
+
+
+def _host_d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_PD)
+
+
+# --------------------------------------------------------------------- context
+def attn_last_error():
+    return load().attn_last_error().decode()
+
+
+def attn_version():
+    return load().attn_version().decode()
+
+
+def attn_config_default():
+    cfg = attn_config()
+    _check(load().attn_config_default(ctypes.byref(cfg)))
+    return cfg
+
+
+def attn_create(cfg=None, stream=None):
+    """Create a context; ``stream`` is a cudaStream_t as int (e.g. torch's cuda_stream)."""
+    h = ctypes.c_void_p()
+    _check(load().attn_create(ctypes.byref(cfg) if cfg is not None else None, stream, ctypes.byref(h)))
+    return h
+
+
+def attn_destroy(ctx):
+    _check(load().attn_destroy(ctx))
+
+
+def attn_set_config(ctx, cfg):
+    _check(load().attn_set_config(ctx, ctypes.byref(cfg)))
+
+
+def attn_get_config(ctx):
+    cfg = attn_config()
+    _check(load().attn_get_config(ctx, ctypes.byref(cfg)))
+    return cfg
+
+
+def attn_sync(ctx):
+    _check(load().attn_sync(ctx))
+
+
+def attn_kernel_launches(ctx):
+    c = ctypes.c_uint64()
+    _check(load().attn_kernel_launches(ctx, ctypes.byref(c)))
+    return c.value
+
+
+# ---------------------------------------------------------------------- models
+def attn_model_tfim(ctx, L, h):
+    m = ctypes.c_void_p()
+    _check(load().attn_model_tfim(ctx, L, h, ctypes.byref(m)))
+    return m
+
+
+def attn_model_tri_heisenberg(ctx, L, J=1.0):
+    m = ctypes.c_void_p()
+    _check(load().attn_model_tri_heisenberg(ctx, L, J, ctypes.byref(m)))
+    return m
+
+
+def attn_model_terms(ctx, n_sites, terms):
+    """``terms``: list of (ascending sites tuple, real 2^k x 2^k operator)."""
+    n = len(terms)
+    ns = np.zeros(n, dtype=np.int32)
+    sites = np.zeros(3 * n, dtype=np.int32)
+    ops = np.zeros(64 * n, dtype=np.float64)
+    for t, (s, op) in enumerate(terms):
+        ns[t] = len(s)
+        sites[3 * t:3 * t + len(s)] = s
+        op = np.asarray(op, dtype=np.float64).reshape(-1)
+        ops[64 * t:64 * t + op.size] = op
+    m = ctypes.c_void_p()
+    _check(load().attn_model_terms(ctx, n_sites, n, ns.ctypes.data_as(_PI), sites.ctypes.data_as(_PI),
+                                   ops.ctypes.data_as(_PD), ctypes.byref(m)))
+    return m
+
+
+def attn_model_destroy(model):
+    _check(load().attn_model_destroy(model))
+
+
+def attn_model_info(model):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().attn_model_info(model, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+# ----------------------------------------------------------------------- state
+def attn_state_create(ctx, model, m, raw_tensors):
+    arrs = [np.ascontiguousarray(t, dtype=np.float64) for t in raw_tensors]
+    ptrs = (_PD * len(arrs))(*[a.ctypes.data_as(_PD) for a in arrs])
+    st = ctypes.c_void_p()
+    _check(load().attn_state_create(ctx, model, m, ptrs, ctypes.byref(st)))
+    return st
+
+
+def attn_state_destroy(st):
+    _check(load().attn_state_destroy(st))
+
+
+def attn_state_info(st):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().attn_state_info(st, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def attn_node_shape(st, node):
+    s = (ctypes.c_int * 3)()
+    _check(load().attn_node_shape(st, node, s))
+    return tuple(s)
+
+
+def attn_node_neighbour(st, node, slot):
+    k, i, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().attn_node_neighbour(st, node, slot, ctypes.byref(k), ctypes.byref(i), ctypes.byref(b)))
+    return k.value, i.value, b.value
+
+
+def attn_node_get(st, node):
+    out = np.empty(attn_node_shape(st, node), dtype=np.float64)
+    _check(load().attn_node_get(st, node, out.ctypes.data_as(_PD)))
+    return out
+
+
+def attn_node_set(st, node, t):
+    a, p = _host_d(t)
+    _check(load().attn_node_set(st, node, p))
+
+
+def attn_node_device_ptr(st, node):
+    p = ctypes.c_void_p()
+    _check(load().attn_node_device_ptr(st, node, ctypes.byref(p)))
+    return p.value
+
+
+def attn_move_centre(st, node):
+    _check(load().attn_move_centre(st, node))
+
+
+def attn_isometry_error(st):
+    e = ctypes.c_double()
+    _check(load().attn_isometry_error(st, ctypes.byref(e)))
+    return e.value
+
+
+# --------------------------------------------------------------- disentanglers
+def attn_de_place(st, max_de):
+    n = ctypes.c_int()
+    _check(load().attn_de_place(st, max_de, ctypes.byref(n)))
+    return n.value
+
+
+def attn_de_sites(st, n):
+    out = np.zeros(2 * max(n, 1), dtype=np.int32)
+    _check(load().attn_de_sites(st, out.ctypes.data_as(_PI)))
+    return [tuple(int(v) for v in out[2 * k:2 * k + 2]) for k in range(n)]
+
+
+def attn_de_set(st, k, u):
+    a, p = _host_d(np.asarray(u).reshape(16))
+    _check(load().attn_de_set(st, k, p))
+
+
+def attn_de_get(st, k):
+    out = np.zeros(16)
+    _check(load().attn_de_get(st, k, out.ctypes.data_as(_PD)))
+    return out.reshape(4, 4)
+
+
+def attn_map_hamiltonian(st):
+    _check(load().attn_map_hamiltonian(st))
+
+
+def attn_hamiltonian_info(st):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().attn_hamiltonian_info(st, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+# ----------------------------------------------------------------------- H_eff
+def attn_heff_create(ctx, m, h_int=(None, None, None), pairs=None, triples=None):
+    """Explicit H_eff from DEVICE operator stacks (torch CUDA float64 tensors).
+
+    ``pairs``: dict kind -> (A stack, B stack) with kind 0 = slots (0,1),
+    1 = (0,2), 2 = (1,2); ``triples``: (O0, O1, O2) stacks or None."""
+    d = attn_heff_desc()
+    for s in range(3):
+        d.m[s] = m[s]
+        d.h_int[s] = _ptr(h_int[s])
+    for k, (a, b) in (pairs or {}).items():
+        d.n_pair[k] = a.shape[0]
+        d.pair_a[k] = _ptr(a)
+        d.pair_b[k] = _ptr(b)
+    if triples is not None:
+        d.n_triple = triples[0].shape[0]
+        for s in range(3):
+            d.triple[s] = _ptr(triples[s])
+    h = ctypes.c_void_p()
+    _check(load().attn_heff_create(ctx, ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def attn_heff_build(st, node):
+    h = ctypes.c_void_p()
+    _check(load().attn_heff_build(st, node, ctypes.byref(h)))
+    return h
+
+
+def attn_heff_destroy(h):
+    _check(load().attn_heff_destroy(h))
+
+
+def attn_heff_info(h):
+    npair = (ctypes.c_int * 3)()
+    nt = ctypes.c_int()
+    fl = ctypes.c_double()
+    _check(load().attn_heff_info(h, npair, ctypes.byref(nt), ctypes.byref(fl)))
+    return tuple(npair), nt.value, fl.value
+
+
+def attn_heff_apply(h, x_dev, y_dev, dtype=ATTN_F64):
+    _check(load().attn_heff_apply(h, _ptr(x_dev), _ptr(y_dev), dtype))
+
+
+def attn_heff_apply_host(h, x, dtype=ATTN_F64):
+    xa, xp = _host_d(x)
+    y = np.empty_like(xa)
+    _check(load().attn_heff_apply_host(h, xp, y.ctypes.data_as(_PD), dtype))
+    return y
+
+
+def attn_eigsolve(h, T_dev):
+    th = ctypes.c_double()
+    it = ctypes.c_int()
+    _check(load().attn_eigsolve(h, _ptr(T_dev), ctypes.byref(th), ctypes.byref(it)))
+    return th.value, it.value
+
+
+# ---------------------------------------------------------------------- sweeps
+def attn_local_step(st, node):
+    e = ctypes.c_double()
+    _check(load().attn_local_step(st, node, ctypes.byref(e)))
+    return e.value
+
+
+def attn_ttn_sweep(st):
+    e = ctypes.c_double()
+    _check(load().attn_ttn_sweep(st, ctypes.byref(e)))
+    return e.value
+
+
+def attn_energy(st):
+    e = ctypes.c_double()
+    _check(load().attn_energy(st, ctypes.byref(e)))
+    return e.value

@@ -1,0 +1,561 @@
+// extern "C" entry points of libattn (see include/attn.h for the contract).
+// Every entry point converts internal exceptions into an attn_status and a
+// thread-local message; nothing throws across the boundary.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <memory>
+
+#include "heff.h"
+#include "state.h"
+
+namespace attn {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+const char* last_error() { return g_err.c_str(); }
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+void DevBuf::reserve(size_t n) {
+  if (n <= bytes && p) return;
+  release();
+  size_t want = std::max<size_t>(n, 256);
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    (void)cudaGetLastError();
+    throw Error{ATTN_ENOMEM, std::string("cudaMalloc of ") + std::to_string(want) + " bytes failed: " +
+                                 cudaGetErrorString(e)};
+  }
+  bytes = want;
+}
+
+}  // namespace attn
+
+using namespace attn;
+
+#define ATTN_TRY try {
+#define ATTN_CATCH                                           \
+  }                                                          \
+  catch (const Error& e) {                                   \
+    set_error("%s", e.msg.c_str());                          \
+    return e.status;                                         \
+  }                                                          \
+  catch (const std::bad_alloc&) {                            \
+    set_error("host allocation failed");                     \
+    return ATTN_ENOMEM;                                      \
+  }                                                          \
+  catch (const std::exception& e) {                          \
+    set_error("%s", e.what());                               \
+    return ATTN_EINVAL;                                      \
+  }                                                          \
+  clear_error();                                             \
+  return ATTN_OK;
+
+#define NEED(p, what) ATTN_REQUIRE((p) != nullptr, ATTN_EINVAL, what " is NULL")
+
+struct attn_model {
+  attn_ctx* ctx;
+  Model M;
+};
+
+extern "C" {
+
+ATTN_API const char* attn_last_error(void) { return last_error(); }
+ATTN_API const char* attn_version(void) { return "attn-gb300 0.1 (sm_103a)"; }
+
+ATTN_API attn_status attn_config_default(attn_config* cfg) {
+  ATTN_TRY
+  NEED(cfg, "cfg");
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->lanczos_depth = 20;
+  cfg->lanczos_tol = 1e-13;
+  cfg->de_max_iter = 20;
+  cfg->de_rel_dev = 1e-12;
+  cfg->s_ttn = 1;
+  cfg->matvec_dtype = ATTN_F64;
+  cfg->refine_steps = 3;
+  cfg->refine_tol = 1e-10;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_create(const attn_config* cfg, void* stream, attn_ctx** out) {
+  ATTN_TRY
+  NEED(out, "out");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    (void)cudaGetLastError();
+    throw Error{ATTN_ECUDA, "no CUDA device available: the library has no CPU fallback"};
+  }
+  auto ctx = std::make_unique<attn_ctx>();
+  if (cfg) ctx->cfg = *cfg; else attn_config_default(&ctx->cfg);
+  ATTN_CHECK_CUDA(cudaGetDevice(&ctx->device));
+  cudaDeviceProp prop;
+  ATTN_CHECK_CUDA(cudaGetDeviceProperties(&prop, ctx->device));
+  ATTN_REQUIRE(prop.major == 10 && prop.minor == 3, ATTN_ECUDA,
+               std::string("libattn is built for sm_103a only; device is ") + prop.name);
+  ctx->num_sms = prop.multiProcessorCount;
+  if (stream) {
+    ctx->stream = (cudaStream_t)stream;
+  } else {
+    ATTN_CHECK_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    ctx->own_stream = true;
+  }
+  ctx->partials.reserve(sizeof(double) * 512 * 64);
+  ctx->scal.reserve(sizeof(double) * 64);
+  *out = ctx.release();
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_destroy(attn_ctx* ctx) {
+  ATTN_TRY
+  if (!ctx) return ATTN_OK;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_set_config(attn_ctx* ctx, const attn_config* cfg) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  NEED(cfg, "cfg");
+  ATTN_REQUIRE(cfg->lanczos_depth >= 1 && cfg->lanczos_depth <= 60, ATTN_EINVAL, "lanczos_depth must be 1..60");
+  ATTN_REQUIRE(cfg->matvec_dtype == ATTN_F64 || cfg->matvec_dtype == ATTN_BF16, ATTN_EUNSUPPORTED,
+               "matvec_dtype must be ATTN_F64 or ATTN_BF16");
+  ctx->cfg = *cfg;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_get_config(attn_ctx* ctx, attn_config* cfg) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  NEED(cfg, "cfg");
+  *cfg = ctx->cfg;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_sync(attn_ctx* ctx) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_kernel_launches(attn_ctx* ctx, uint64_t* count) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  NEED(count, "count");
+  *count = ctx->launches;
+  ATTN_CATCH
+}
+
+// ------------------------------------------------------------------ models
+ATTN_API attn_status attn_model_tfim(attn_ctx* ctx, int L, double h, attn_model** out) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  NEED(out, "out");
+  auto m = std::make_unique<attn_model>();
+  m->ctx = ctx;
+  build_tfim(m->M, L, h);
+  *out = m.release();
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_model_tri_heisenberg(attn_ctx* ctx, int L, double J, attn_model** out) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  NEED(out, "out");
+  auto m = std::make_unique<attn_model>();
+  m->ctx = ctx;
+  build_tri_heisenberg(m->M, L, J);
+  *out = m.release();
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_model_terms(attn_ctx* ctx, int n_sites, int n_terms, const int* nsites, const int* sites,
+                                      const double* ops, attn_model** out) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  NEED(out, "out");
+  ATTN_REQUIRE(n_terms >= 0, ATTN_EINVAL, "n_terms < 0");
+  if (n_terms) {
+    NEED(nsites, "term_nsites");
+    NEED(sites, "term_sites");
+    NEED(ops, "term_ops");
+  }
+  auto m = std::make_unique<attn_model>();
+  m->ctx = ctx;
+  build_generic(m->M, n_sites, n_terms, nsites, sites, ops);
+  *out = m.release();
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_model_destroy(attn_model* model) {
+  ATTN_TRY
+  delete model;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_model_info(const attn_model* model, int* n_sites, int* n_terms) {
+  ATTN_TRY
+  NEED(model, "model");
+  if (n_sites) *n_sites = model->M.n_sites;
+  if (n_terms) *n_terms = (int)model->M.terms.size();
+  ATTN_CATCH
+}
+
+// ------------------------------------------------------------------- state
+ATTN_API attn_status attn_state_create(attn_ctx* ctx, const attn_model* model, int m, const double* const* raw,
+                                       attn_state** out) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  NEED(model, "model");
+  NEED(raw, "raw_host");
+  NEED(out, "out");
+  auto st = std::make_unique<attn_state>();
+  st->ctx = ctx;
+  st->model = model->M;
+  st->tree.build(model->M.n_sites, m);
+  for (int n = 0; n < st->tree.n_nodes; ++n) {
+    NEED(raw[n], "raw_host[node]");
+    for (long i = 0; i < st->vol(n); ++i)
+      ATTN_REQUIRE(std::isfinite(raw[n][i]), ATTN_ENONFINITE, "non-finite initial tensor entry");
+  }
+  st->init_from_raw(raw);
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  *out = st.release();
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_state_destroy(attn_state* st) {
+  ATTN_TRY
+  if (!st) return ATTN_OK;
+  cudaStreamSynchronize(st->ctx->stream);
+  delete st;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_state_info(attn_state* st, int* n_nodes, int* centre, int* n_layers) {
+  ATTN_TRY
+  NEED(st, "state");
+  if (n_nodes) *n_nodes = st->tree.n_nodes;
+  if (centre) *centre = st->centre;
+  if (n_layers) *n_layers = st->tree.nL;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_node_shape(attn_state* st, int node, int shape[3]) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(shape, "shape");
+  ATTN_REQUIRE(node >= 0 && node < st->tree.n_nodes, ATTN_EINVAL, "node out of range");
+  for (int s = 0; s < 3; ++s) shape[s] = st->dim(node, s);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_node_neighbour(attn_state* st, int node, int slot, int* kind, int* idx, int* back) {
+  ATTN_TRY
+  NEED(st, "state");
+  ATTN_REQUIRE(node >= 0 && node < st->tree.n_nodes && slot >= 0 && slot < 3, ATTN_EINVAL, "node/slot out of range");
+  const Tree::Nbr& nb = st->tree.nbr[3 * node + slot];
+  if (kind) *kind = nb.kind;
+  if (idx) *idx = nb.idx;
+  if (back) *back = nb.back;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_node_get(attn_state* st, int node, double* host_out) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(host_out, "host_out");
+  ATTN_REQUIRE(node >= 0 && node < st->tree.n_nodes, ATTN_EINVAL, "node out of range");
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(host_out, st->tensor(node), sizeof(double) * st->vol(node), cudaMemcpyDeviceToHost,
+                                  st->ctx->stream));
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_node_set(attn_state* st, int node, const double* host_in) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(host_in, "host_in");
+  ATTN_REQUIRE(node >= 0 && node < st->tree.n_nodes, ATTN_EINVAL, "node out of range");
+  for (long i = 0; i < st->vol(node); ++i)
+    ATTN_REQUIRE(std::isfinite(host_in[i]), ATTN_ENONFINITE, "non-finite tensor entry");
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(st->tensor(node), host_in, sizeof(double) * st->vol(node), cudaMemcpyHostToDevice,
+                                  st->ctx->stream));
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  st->invalidate_from(node);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_node_device_ptr(attn_state* st, int node, double** dev_ptr) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(dev_ptr, "dev_ptr");
+  ATTN_REQUIRE(node >= 0 && node < st->tree.n_nodes, ATTN_EINVAL, "node out of range");
+  *dev_ptr = st->tensor(node);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_move_centre(attn_state* st, int node) {
+  ATTN_TRY
+  NEED(st, "state");
+  st->move_centre(node);
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_isometry_error(attn_state* st, double* err) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(err, "err");
+  *err = st->isometry_error();
+  ATTN_CATCH
+}
+
+// ------------------------------------------------------------ disentanglers
+ATTN_API attn_status attn_de_place(attn_state* st, int max_de, int* n_placed) {
+  ATTN_TRY
+  NEED(st, "state");
+  ATTN_REQUIRE(max_de >= 0, ATTN_EINVAL, "max_de < 0");
+  st->des = place_disentanglers(st->tree, st->model, max_de);
+  st->us.assign(st->des.size(), std::vector<double>(16, 0.0));
+  for (auto& u : st->us)
+    for (int i = 0; i < 4; ++i) u[i * 5] = 1.0;
+  st->mapped_ready = false;
+  if (n_placed) *n_placed = (int)st->des.size();
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_de_sites(attn_state* st, int* pairs) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(pairs, "pairs_out");
+  for (size_t k = 0; k < st->des.size(); ++k) {
+    pairs[2 * k] = st->des[k].first;
+    pairs[2 * k + 1] = st->des[k].second;
+  }
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_de_set(attn_state* st, int k, const double* u16) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(u16, "u16");
+  ATTN_REQUIRE(k >= 0 && k < (int)st->des.size(), ATTN_EINVAL, "disentangler index out of range");
+  double err = 0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0;
+      for (int q = 0; q < 4; ++q) s += u16[q * 4 + i] * u16[q * 4 + j];
+      err = std::max(err, std::fabs(s - (i == j ? 1.0 : 0.0)));
+    }
+  ATTN_REQUIRE(err < 1e-10, ATTN_ENOTISOMETRIC, "disentangler is not orthogonal (|u^T u - 1| >= 1e-10)");
+  st->us[k].assign(u16, u16 + 16);
+  st->mapped_ready = false;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_de_get(attn_state* st, int k, double* u16) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(u16, "u16");
+  ATTN_REQUIRE(k >= 0 && k < (int)st->des.size(), ATTN_EINVAL, "disentangler index out of range");
+  std::memcpy(u16, st->us[k].data(), 16 * sizeof(double));
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_map_hamiltonian(attn_state* st) {
+  ATTN_TRY
+  NEED(st, "state");
+  st->set_products();
+  for (int s = 0; s < 3; ++s) st->get_env(st->centre, s);
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_hamiltonian_info(attn_state* st, int* n_terms, int* n_products) {
+  ATTN_TRY
+  NEED(st, "state");
+  if (n_terms) *n_terms = (int)st->mapped.size();
+  if (n_products) *n_products = (int)st->prods.size();
+  ATTN_CATCH
+}
+
+// -------------------------------------------------------------------- H_eff
+ATTN_API attn_status attn_heff_create(attn_ctx* ctx, const attn_heff_desc* d, attn_heff** out) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  NEED(d, "desc");
+  NEED(out, "out");
+  auto h = std::make_unique<attn_heff>();
+  h->ctx = ctx;
+  for (int s = 0; s < 3; ++s) {
+    ATTN_REQUIRE(d->m[s] >= 1 && d->m[s] <= 4096, ATTN_EINVAL, "link dimension must be 1..4096");
+    h->m[s] = d->m[s];
+  }
+  h->V = (long)d->m[0] * d->m[1] * d->m[2];
+  for (int s = 0; s < 3; ++s) {
+    if (!d->h_int[s]) continue;
+    const long sz = (long)d->m[s] * d->m[s];
+    h->has_hint[s] = true;
+    h->hint[s].reserve(sizeof(double) * sz);
+    copy_f64(ctx, h->hint[s].as<double>(), d->h_int[s], sz);
+  }
+  for (int k = 0; k < 3; ++k) {
+    ATTN_REQUIRE(d->n_pair[k] >= 0, ATTN_EINVAL, "n_pair < 0");
+    h->npair[k] = d->n_pair[k];
+    if (!d->n_pair[k]) continue;
+    NEED(d->pair_a[k], "pair_a");
+    NEED(d->pair_b[k], "pair_b");
+    const int p = kPairP[k], q = kPairQ[k];
+    const long na = (long)d->n_pair[k] * d->m[p] * d->m[p], nb = (long)d->n_pair[k] * d->m[q] * d->m[q];
+    h->pa[k].reserve(sizeof(double) * na);
+    h->pb[k].reserve(sizeof(double) * nb);
+    copy_f64(ctx, h->pa[k].as<double>(), d->pair_a[k], na);
+    copy_f64(ctx, h->pb[k].as<double>(), d->pair_b[k], nb);
+  }
+  ATTN_REQUIRE(d->n_triple >= 0, ATTN_EINVAL, "n_triple < 0");
+  h->ntrip = d->n_triple;
+  if (h->ntrip) {
+    for (int s = 0; s < 3; ++s) {
+      NEED(d->triple[s], "triple");
+      const long n = (long)h->ntrip * d->m[s] * d->m[s];
+      h->tr[s].reserve(sizeof(double) * n);
+      copy_f64(ctx, h->tr[s].as<double>(), d->triple[s], n);
+    }
+  }
+  *out = h.release();
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_heff_build(attn_state* st, int node, attn_heff** out) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(out, "out");
+  ATTN_REQUIRE(node >= 0 && node < st->tree.n_nodes, ATTN_EINVAL, "node out of range");
+  *out = st->build_heff(node);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_heff_destroy(attn_heff* h) {
+  ATTN_TRY
+  if (!h) return ATTN_OK;
+  cudaStreamSynchronize(h->ctx->stream);
+  delete h;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_heff_info(attn_heff* h, int n_pair[3], int* n_triple, double* flops) {
+  ATTN_TRY
+  NEED(h, "heff");
+  if (n_pair)
+    for (int k = 0; k < 3; ++k) n_pair[k] = h->npair[k];
+  if (n_triple) *n_triple = h->ntrip;
+  if (flops) *flops = h->flops();
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_heff_apply(attn_heff* h, const double* x, double* y, attn_dtype dtype) {
+  ATTN_TRY
+  NEED(h, "heff");
+  NEED(x, "x_dev");
+  NEED(y, "y_dev");
+  ATTN_REQUIRE(x != y, ATTN_EINVAL, "x and y must be distinct buffers");
+  if (dtype == ATTN_F64) h->apply_f64(x, y);
+  else if (dtype == ATTN_BF16) h->apply_bf16(x, y);
+  else throw Error{ATTN_EUNSUPPORTED, "dtype must be ATTN_F64 or ATTN_BF16"};
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_heff_apply_host(attn_heff* h, const double* xh, double* yh, attn_dtype dtype) {
+  ATTN_TRY
+  NEED(h, "heff");
+  NEED(xh, "x_host");
+  NEED(yh, "y_host");
+  attn_ctx* ctx = h->ctx;
+  ctx->ws[2].reserve(sizeof(double) * 2 * h->V);
+  double* xd = ctx->ws[2].as<double>();
+  double* yd = xd + h->V;
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(xd, xh, sizeof(double) * h->V, cudaMemcpyHostToDevice, ctx->stream));
+  if (dtype == ATTN_F64) h->apply_f64(xd, yd);
+  else if (dtype == ATTN_BF16) h->apply_bf16(xd, yd);
+  else throw Error{ATTN_EUNSUPPORTED, "dtype must be ATTN_F64 or ATTN_BF16"};
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(yh, yd, sizeof(double) * h->V, cudaMemcpyDeviceToHost, ctx->stream));
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, int* iters) {
+  ATTN_TRY
+  NEED(h, "heff");
+  NEED(T_dev, "T_dev");
+  NEED(theta, "theta");
+  attn_ctx* ctx = h->ctx;
+  const attn_config& cfg = ctx->cfg;
+  LanczosWork w;
+  const attn_dtype dt = cfg.matvec_dtype;
+  MatVec lo = [&](const double* a, double* b) {
+    if (dt == ATTN_BF16) h->apply_bf16(a, b); else h->apply_f64(a, b);
+  };
+  MatVec hi = [&](const double* a, double* b) { h->apply_f64(a, b); };
+  LanczosResult r = lanczos_lowest(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, w);
+  int it = r.iters;
+  if (dt != ATTN_F64 && cfg.refine_steps > 0) {
+    r = lanczos_lowest(ctx, hi, T_dev, h->V, cfg.refine_steps + 1, cfg.refine_tol, w);
+    it += r.iters;
+  }
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  *theta = r.theta;
+  if (iters) *iters = it;
+  ATTN_CATCH
+}
+
+// ----------------------------------------------------------- sweep drivers
+ATTN_API attn_status attn_local_step(attn_state* st, int node, double* energy) {
+  ATTN_TRY
+  NEED(st, "state");
+  double e = st->local_step(node);
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  if (energy) *energy = e;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_ttn_sweep(attn_state* st, double* energy) {
+  ATTN_TRY
+  NEED(st, "state");
+  double e = 0;
+  for (int n : st->tree.post_order()) e = st->local_step(n);
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  if (energy) *energy = e;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_energy(attn_state* st, double* energy) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(energy, "energy");
+  *energy = st->energy();
+  ATTN_CATCH
+}
+
+}  // extern "C"

@@ -1,0 +1,245 @@
+// FP64 CUDA-core contraction kernels.
+//
+// One generic batched, grouped, fully strided GEMM covers every FP64
+// contraction of the method: the two stages of each H_eff product
+// (Sec. 4.4.2, Fig. eff-op-cost), the renormalisation T^T (O (x) O) T
+// (Fig. eff-op) and the Gram/projection products of QR. GB300's FP64 rate is
+// low (FMA-bound at about 1.2 TFLOP/s), so the kernel is a plain
+// shared-memory-tiled register-blocked GEMM: 64x64 output tile per 256-thread
+// CTA, 4x4 accumulators per thread, K tile 16; loads pick the coalesced
+// mapping from the unit stride of each operand.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "attn_internal.h"
+
+namespace attn {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+__global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const long nb = (long)g.Bhi * g.Blo;
+  const bool a_kfast = (g.aK == 1);
+  const bool b_nfast = (g.bN == 1);
+  for (long bz = blockIdx.z; bz < nb; bz += gridDim.z) {
+    const long bh = bz / g.Blo, bl = bz % g.Blo;
+    const double* Ab = g.A + bh * g.aBhi + bl * g.aBlo;
+    const double* Bb = g.B + bh * g.bBhi + bl * g.bBlo;
+    double* Cb = g.C + bh * g.cBhi + bl * g.cBlo;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int gg = 0; gg < g.G; ++gg) {
+      const double* Ag = Ab + gg * g.aG;
+      const double* Bg = Bb + gg * g.bG;
+      for (int k0 = 0; k0 < g.K; k0 += BK) {
+#pragma unroll
+        for (int q = 0; q < (BM * BK) / NT; ++q) {
+          int e = tid + q * NT;
+          int i, k;
+          if (a_kfast) { k = e % BK; i = e / BK; } else { i = e % BM; k = e / BM; }
+          int gi = m0 + i, gk = k0 + k;
+          As[k][i] = (gi < g.M && gk < g.K) ? Ag[gi * g.aM + gk * g.aK] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < (BN * BK) / NT; ++q) {
+          int e = tid + q * NT;
+          int j, k;
+          if (b_nfast) { j = e % BN; k = e / BN; } else { k = e % BK; j = e / BK; }
+          int gj = n0 + j, gk = k0 + k;
+          Bs[k][j] = (gj < g.N && gk < g.K) ? Bg[gk * g.bK + gj * g.bN] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+          double a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int gi = m0 + ty + 16 * i;
+      if (gi >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int gj = n0 + tx + 16 * j;
+        if (gj >= g.N) continue;
+        double* c = Cb + gi * g.cM + gj * g.cN;
+        double v = g.alpha * acc[i][j];
+        *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
+      }
+    }
+  }
+}
+
+__global__ void fill_kernel(double* p, size_t n, double v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+__global__ void axpy_kernel(double* y, const double* x, size_t n, double a) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+
+__global__ void copy_kernel(double* d, const double* s, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) d[i] = s[i];
+}
+
+__global__ void gather_kernel(double* dst, const double* src, const int* idx, int R, long len) {
+  long total = (long)R * len;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    long r = e / len, o = e % len;
+    dst[e] = src[(long)idx[r] * len + o];
+  }
+}
+
+__global__ void identity_kernel(double* dst, int R, int m) {
+  long total = (long)R * m * m;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    long o = e % ((long)m * m);
+    dst[e] = (o / m == o % m) ? 1.0 : 0.0;
+  }
+}
+
+// Deterministic two-pass dot product: per-block partials then one block sums them.
+__global__ void dot_partial_kernel(const double* x, const double* y, size_t n, double* part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    s = fma(x[i], y[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+__global__ void sum_partials_kernel(const double* part, int n, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *out = s;
+  }
+}
+
+inline int grid_for(size_t n, int threads = 256, int cap = 4096) {
+  size_t b = (n + threads - 1) / threads;
+  return (int)std::max<size_t>(1, std::min<size_t>(b, (size_t)cap));
+}
+
+}  // namespace
+
+void gemm_f64(attn_ctx* ctx, const GemmF64& g) {
+  if (g.M <= 0 || g.N <= 0 || g.Bhi <= 0 || g.Blo <= 0) return;
+  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, (unsigned)std::min<long>((long)g.Bhi * g.Blo, 65535));
+  ATTN_REQUIRE(grid.y <= 65535, ATTN_EUNSUPPORTED, "GEMM M too large");
+  gemm_f64_kernel<<<grid, NT, 0, ctx->stream>>>(g);
+  ctx->launches++;
+  ATTN_CHECK_CUDA(cudaGetLastError());
+}
+
+void mode_product_f64(attn_ctx* ctx, const int d[3], int slot, const double* mats, int R, const double* in,
+                      long in_stride, double* out, double beta) {
+  const long V = (long)d[0] * d[1] * d[2];
+  const long ms = (long)d[slot] * d[slot];
+  GemmF64 g;
+  g.beta = beta;
+  if (slot == 0) {
+    // out_r[i, (bc)] = sum_j M_r[i, j] in_r[j, (bc)]
+    g.M = d[0]; g.N = d[1] * d[2]; g.K = d[0];
+    g.A = mats; g.aM = d[0]; g.aK = 1; g.aBhi = ms;
+    g.B = in; g.bK = (long)d[1] * d[2]; g.bN = 1; g.bBhi = in_stride;
+    g.C = out; g.cM = (long)d[1] * d[2]; g.cN = 1; g.cBhi = V;
+    g.Bhi = R; g.Blo = 1;
+  } else if (slot == 1) {
+    // out_r[a][i, c] = sum_j M_r[i, j] in_r[a][j, c]
+    g.M = d[1]; g.N = d[2]; g.K = d[1];
+    g.A = mats; g.aM = d[1]; g.aK = 1; g.aBhi = ms; g.aBlo = 0;
+    g.B = in; g.bK = d[2]; g.bN = 1; g.bBhi = in_stride; g.bBlo = (long)d[1] * d[2];
+    g.C = out; g.cM = d[2]; g.cN = 1; g.cBhi = V; g.cBlo = (long)d[1] * d[2];
+    g.Bhi = R; g.Blo = d[0];
+  } else {
+    // out_r[(ab), i] = sum_j in_r[(ab), j] M_r[i, j]
+    g.M = d[0] * d[1]; g.N = d[2]; g.K = d[2];
+    g.A = in; g.aM = d[2]; g.aK = 1; g.aBhi = in_stride;
+    g.B = mats; g.bK = 1; g.bN = d[2]; g.bBhi = ms;
+    g.C = out; g.cM = d[2]; g.cN = 1; g.cBhi = V;
+    g.Bhi = R; g.Blo = 1;
+  }
+  gemm_f64(ctx, g);
+}
+
+void fill_f64(attn_ctx* ctx, double* p, size_t n, double v) {
+  if (!n) return;
+  fill_kernel<<<grid_for(n), 256, 0, ctx->stream>>>(p, n, v);
+  ctx->launches++;
+  ATTN_CHECK_CUDA(cudaGetLastError());
+}
+
+void copy_f64(attn_ctx* ctx, double* d, const double* s, size_t n) {
+  if (!n) return;
+  copy_kernel<<<grid_for(n), 256, 0, ctx->stream>>>(d, s, n);
+  ctx->launches++;
+  ATTN_CHECK_CUDA(cudaGetLastError());
+}
+
+void axpy_f64(attn_ctx* ctx, double* y, const double* x, size_t n, double a) {
+  if (!n) return;
+  axpy_kernel<<<grid_for(n), 256, 0, ctx->stream>>>(y, x, n, a);
+  ctx->launches++;
+  ATTN_CHECK_CUDA(cudaGetLastError());
+}
+
+void gather_rows_f64(attn_ctx* ctx, double* dst, const double* src, const int* idx, int R, long len) {
+  if (R <= 0 || len <= 0) return;
+  gather_kernel<<<grid_for((size_t)R * len), 256, 0, ctx->stream>>>(dst, src, idx, R, len);
+  ctx->launches++;
+  ATTN_CHECK_CUDA(cudaGetLastError());
+}
+
+void identity_stack_f64(attn_ctx* ctx, double* dst, int R, int m) {
+  if (R <= 0) return;
+  identity_kernel<<<grid_for((size_t)R * m * m), 256, 0, ctx->stream>>>(dst, R, m);
+  ctx->launches++;
+  ATTN_CHECK_CUDA(cudaGetLastError());
+}
+
+void dot_f64(attn_ctx* ctx, const double* x, const double* y, size_t n, double* out_dev) {
+  const int blocks = 256;
+  ctx->partials.reserve(sizeof(double) * blocks);
+  double* part = ctx->partials.as<double>();
+  dot_partial_kernel<<<blocks, 256, 0, ctx->stream>>>(x, y, n, part);
+  sum_partials_kernel<<<1, 256, 0, ctx->stream>>>(part, blocks, out_dev);
+  ctx->launches += 2;
+  ATTN_CHECK_CUDA(cudaGetLastError());
+}
+
+}  // namespace attn

@@ -1,0 +1,36 @@
+// Effective-Hamiltonian object (internal).
+#pragma once
+
+#include "attn_internal.h"
+
+// Pair kinds: 0 = slots (0,1) with slice slot 2; 1 = (0,2) slice 1; 2 = (1,2) slice 0.
+static const int kPairP[3] = {0, 0, 1};
+static const int kPairQ[3] = {1, 2, 2};
+static const int kPairS[3] = {2, 1, 0};
+
+struct attn_heff {
+  attn_ctx* ctx = nullptr;
+  int m[3] = {0, 0, 0};
+  long V = 0;
+  bool has_hint[3] = {false, false, false};
+  attn::DevBuf hint[3];   // [m_l][m_l] FP64
+  int npair[3] = {0, 0, 0};
+  attn::DevBuf pa[3], pb[3];  // FP64 stacks [n][m_p][m_p], [n][m_q][m_q]
+  int ntrip = 0;
+  attn::DevBuf tr[3];     // FP64 stacks [n][m_l][m_l]
+  // Low-precision tensor-core copies (built on first BF16 apply).
+  bool tc_ready = false;
+  void* tc = nullptr;     // opaque, owned by heff_tc.cu
+  double flops() const;
+  void apply_f64(const double* x, double* y);
+  void apply_bf16(const double* x, double* y);
+  ~attn_heff();
+};
+
+namespace attn {
+void tc_release(attn_heff* h);
+bool tc_supported(const attn_heff* h);
+int tc_error(attn_heff* h);
+// y += sum_{r<R} A_r x_p W_r with W_r per-product tensors (stride V), FP64.
+void accumulate_slot_f64(attn_ctx* ctx, const int d[3], int p, const double* A, int R, const double* W, double* y);
+}  // namespace attn

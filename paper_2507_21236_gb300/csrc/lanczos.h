@@ -1,0 +1,35 @@
+// Lanczos and vector kernels (internal).
+#pragma once
+
+#include <functional>
+
+#include "attn_internal.h"
+
+namespace attn {
+
+using MatVec = std::function<void(const double* x, double* y)>;
+
+struct LanczosWork {
+  DevBuf basis, wvec, scal;
+};
+
+struct LanczosResult {
+  double theta;
+  int iters;
+  double resid;
+  bool converged;
+};
+
+// Lowest Ritz pair of the symmetric operator `apply` starting from x (device,
+// length V). On return x holds the unit-norm Ritz vector.
+LanczosResult lanczos_lowest(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol,
+                             LanczosWork& w);
+
+// out[i] = <basis_i, w> for i < nvec (deterministic two-pass reduction); accum[i] += out[i] if given.
+void multi_dot(attn_ctx* ctx, const double* basis, int nvec, long V, const double* w, double* out, double* accum);
+void multi_axpy_dev(attn_ctx* ctx, double* w, const double* basis, const double* coef, int nvec, long V, double sign);
+void combine_dev(attn_ctx* ctx, double* out, const double* basis, const double* coef, int nvec, long V);
+// dst = src / ||src||; nrm_sq_dev receives ||src||^2.
+void normalise_dev(attn_ctx* ctx, double* dst, const double* src, long V, double* nrm_sq_dev);
+
+}  // namespace attn

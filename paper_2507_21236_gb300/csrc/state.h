@@ -1,0 +1,61 @@
+// TTN state with per-link effective operators (internal).
+#pragma once
+
+#include <utility>
+#include <vector>
+
+#include "attn_internal.h"
+#include "heff.h"
+#include "lanczos.h"
+#include "qr.h"
+
+namespace attn {
+
+// Operators on link (n, slot) as seen from node n (Sec. 3.3.2): the summed
+// operator of every product lying entirely behind the link (hint) and one
+// renormalised operator per product with sites on both sides (open).
+struct Env {
+  int dim = 0;
+  bool valid = false;
+  bool has_hint = false;
+  DevBuf hint;                         // dim x dim
+  std::vector<int> open;               // product ids, in stacking order
+  std::vector<std::pair<int, int>> pos;  // (product id, index in ops), sorted by id
+  DevBuf ops;                          // [open.size()][dim][dim]
+  int find(int q) const;               // index in ops or -1
+};
+
+}  // namespace attn
+
+struct attn_state {
+  attn_ctx* ctx = nullptr;
+  attn::Model model;
+  attn::Tree tree;
+  std::vector<attn::DevBuf> T;  // node tensors [d0][d1][d2] FP64
+  int centre = 0;
+  std::vector<std::pair<int, int>> des;
+  std::vector<std::vector<double>> us;
+  std::vector<attn::Term> mapped;
+  std::vector<attn::Prod> prods;
+  std::vector<attn::Env> env;  // [node*3 + slot]
+  bool mapped_ready = false;
+  attn::QRWork qrw;
+  attn::LanczosWork lw, lw2;
+  attn::DevBuf colbuf, rbuf, tmpT, idxbuf, opsA, opsB, rw1, rw2;
+
+  int dim(int n, int s) const { return tree.shape[3 * n + s]; }
+  long vol(int n) const { return (long)dim(n, 0) * dim(n, 1) * dim(n, 2); }
+  double* tensor(int n) { return T[n].as<double>(); }
+
+  void init_from_raw(const double* const* raw);
+  void invalidate_from(int changed_node);
+  void move_centre(int target);
+  void set_products();         // map terms through the disentanglers and split
+  attn::Env& get_env(int n, int slot);
+  void build_physical_env(int n, int slot);
+  void renormalise_into(int n, int slot);
+  attn_heff* build_heff(int n);
+  double energy();
+  double local_step(int n);
+  double isometry_error();
+};
