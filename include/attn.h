@@ -168,11 +168,17 @@ ATTN_API attn_status attn_de_sites(attn_state* st, int* pairs_out);
 ATTN_API attn_status attn_de_set(attn_state* st, int k, const double* u16);
 ATTN_API attn_status attn_de_get(attn_state* st, int k, double* u16);
 /* Map the Hamiltonian through the disentangler layer, H' = D^T H D
- * (Sec. 4.3, Algorithm 1), split the mapped terms into rank-1 products and
- * rebuild all effective operators towards the current centre (Sec. 3.3.2). */
+ * (Sec. 4.3, Algorithm 1), and split the mapped terms into rank-1 products.
+ * All effective operators are invalidated; they are rebuilt on the GPU on
+ * demand (Sec. 3.3.2) by the calls that need them. */
 ATTN_API attn_status attn_map_hamiltonian(attn_state* st);
 /* Number of mapped terms and rank-1 products of the current H'. */
 ATTN_API attn_status attn_hamiltonian_info(attn_state* st, int* n_terms, int* n_products);
+/* Structure of H_eff at `node` (host bookkeeping only, no device work): the
+ * number of rank-1 products of H' spanning link pairs (0,1), (0,2), (1,2),
+ * all three links, and lying behind a single link (summed into that link's
+ * internal operator), in counts[0..4]. Requires attn_map_hamiltonian. */
+ATTN_API attn_status attn_heff_counts(attn_state* st, int node, int counts[5]);
 
 /* -------------------------------------------------------------------- H_eff */
 

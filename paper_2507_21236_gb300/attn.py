@@ -75,6 +75,7 @@ _SIGS = {
     "attn_de_get": [_P, _I, _PD],
     "attn_map_hamiltonian": [_P],
     "attn_hamiltonian_info": [_P, _PI, _PI],
+    "attn_heff_counts": [_P, _I, _PI],
     "attn_heff_create": [_P, ctypes.POINTER(attn_heff_desc), _PP],
     "attn_heff_build": [_P, _I, _PP],
     "attn_heff_destroy": [_P],
@@ -315,6 +316,12 @@ def attn_hamiltonian_info(st):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(load().attn_hamiltonian_info(st, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def attn_heff_counts(st, node):
+    c = (ctypes.c_int * 5)()
+    _check(load().attn_heff_counts(st, node, c))
+    return tuple(c)
 
 
 # ----------------------------------------------------------------------- H_eff

@@ -388,8 +388,27 @@ ATTN_API attn_status attn_map_hamiltonian(attn_state* st) {
   ATTN_TRY
   NEED(st, "state");
   st->set_products();
-  for (int s = 0; s < 3; ++s) st->get_env(st->centre, s);
-  ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_heff_counts(attn_state* st, int node, int counts[5]) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(counts, "counts");
+  ATTN_REQUIRE(node >= 0 && node < st->tree.n_nodes, ATTN_EINVAL, "node out of range");
+  ATTN_REQUIRE(st->mapped_ready, ATTN_EINVAL, "Hamiltonian not mapped yet (call attn_map_hamiltonian)");
+  for (int i = 0; i < 5; ++i) counts[i] = 0;
+  for (const Prod& p : st->prods) {
+    int mask = 0;
+    for (int a = 0; a < p.n; ++a)
+      for (int s = 0; s < 3; ++s)
+        if (st->tree.behind(node, s, p.site[a])) mask |= 1 << s;
+    if (mask == 3) counts[0]++;
+    else if (mask == 5) counts[1]++;
+    else if (mask == 6) counts[2]++;
+    else if (mask == 7) counts[3]++;
+    else counts[4]++;
+  }
   ATTN_CATCH
 }
 

@@ -287,6 +287,11 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
       }
     }
     mma_commit(bar(D2FULL));
+    // every MMA this thread issued must finish before TMEM can be freed
+    {
+      long long t0 = clock64();
+      while (!mbar_try_wait(bar(D2FULL), 0) && clock64() - t0 < kWaitCycles) {}
+    }
   } else if (warp >= 4) {
     // ---- conversion D1 -> Z^T (bf16, swizzled) and the epilogue
     const int q4 = warp & 3;

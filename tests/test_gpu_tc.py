@@ -1,0 +1,162 @@
+"""BF16 tensor-core H_eff (tcgen05) against the FP64 oracle.
+
+Tolerance, derived from the arithmetic: every product term sees at most four
+BF16 roundings (x, A_r, B_r and the stage-1 result Z_r), each with unit
+roundoff u = 2^-8, plus FP32 accumulation over K = Q (stage 1) and R*P
+(stage 2) terms. Componentwise,
+    |y_bf16 - y| <= ((1+u)^4 - 1 + (Q + R*P + 2) * 2^-24) * y_abs,
+with y_abs the same contraction applied to |x| and the entrywise absolute
+operators. The test checks that bound elementwise, plus a typical-size check
+on the normwise error.
+"""
+import numpy as np
+import pytest
+
+from inputs import random_operators, random_vector
+from oracle.ttn import heff_apply_ops, heff_sample_ops
+from tests.gpu_util import dev, host, lib_and_ctx
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -8
+KINDS = {0: (0, 1), 1: (0, 2), 2: (1, 2)}
+
+
+def _bound(shape, counts):
+    R = max(counts) + 3
+    P = max(shape)
+    return (1 + U) ** 4 - 1 + (P + R * P + 2) * 2.0 ** -24
+
+
+def _case(shape, counts, seed, with_hint=True):
+    h = tuple(random_operators(1, m, seed, 10 + s)[0] if with_hint else None for s, m in enumerate(shape))
+    pairs = {k: (random_operators(counts[k], shape[p], seed, 20 + 2 * k),
+                 random_operators(counts[k], shape[q], seed, 21 + 2 * k))
+             for k, (p, q) in KINDS.items() if counts[k]}
+    return h, pairs
+
+
+@pytest.mark.parametrize("shape,counts", [
+    ((128, 128, 128), (3, 2, 2)),
+    ((64, 64, 64), (10, 6, 6)),
+    ((16, 16, 128), (12, 8, 8)),
+    ((32, 48, 80), (5, 4, 3)),
+    ((128, 128, 128), (0, 0, 5)),   # one kind only
+])
+def test_bf16_heff_within_rounding_bound(shape, counts):
+    attn, ctx = lib_and_ctx()
+    h, pairs = _case(shape, counts, seed=3)
+    x = random_vector(shape, 9)
+    H = attn.attn_heff_create(ctx, shape, [dev(a) for a in h], {k: (dev(a), dev(b)) for k, (a, b) in pairs.items()})
+    import torch
+    xd = dev(x)
+    yd = torch.full_like(xd, float("nan"))
+    attn.attn_heff_apply(H, xd, yd, attn.ATTN_BF16)
+    y = host(yd)
+    op = {KINDS[k]: v for k, v in pairs.items()}
+    y64 = heff_apply_ops(x, h, op)
+    yabs = heff_apply_ops(np.abs(x), tuple(np.abs(a) for a in h),
+                          {k: (np.abs(a), np.abs(b)) for k, (a, b) in op.items()})
+    assert np.isfinite(y).all()
+    b = _bound(shape, counts)
+    viol = np.abs(y - y64) - b * yabs
+    assert viol.max() <= 1e-30, (float(viol.max()), b)
+    # typical error is far below the worst-case bound
+    assert np.linalg.norm(y - y64) / np.linalg.norm(yabs) < U
+    attn.attn_heff_destroy(H)
+    attn.attn_destroy(ctx)
+
+
+def test_bf16_heff_full_size_many_products():
+    """[128]^3 with ~300 products per kind (the size of the 32x32, m = 128 top nodes), sampled."""
+    shape = (128, 128, 128)
+    counts = (300, 120, 120)
+    attn, ctx = lib_and_ctx()
+    h, pairs = _case(shape, counts, seed=21)
+    x = random_vector(shape, 4)
+    H = attn.attn_heff_create(ctx, shape, [dev(a) for a in h], {k: (dev(a), dev(b)) for k, (a, b) in pairs.items()})
+    import torch
+    xd = dev(x)
+    yd = torch.empty_like(xd)
+    for _ in range(2):  # second call reuses the built tensor-core state
+        attn.attn_heff_apply(H, xd, yd, attn.ATTN_BF16)
+    y = host(yd)
+    op = {KINDS[k]: v for k, v in pairs.items()}
+    rng = np.random.default_rng(1)
+    idx = [tuple(int(v) for v in rng.integers(0, 128, 3)) for _ in range(16)]
+    ref = heff_sample_ops(x, idx, h, op)
+    absref = heff_sample_ops(np.abs(x), idx, tuple(np.abs(a) for a in h),
+                             {k: (np.abs(a), np.abs(b)) for k, (a, b) in op.items()})
+    got = np.array([y[i] for i in idx])
+    assert np.all(np.abs(got - ref) <= _bound(shape, counts) * absref)
+    attn.attn_heff_destroy(H)
+    attn.attn_destroy(ctx)
+
+
+def test_bf16_unsupported_shape_is_an_error():
+    attn, ctx = lib_and_ctx()
+    H = attn.attn_heff_create(ctx, (2, 2, 4))
+    import torch
+    xd = dev(np.ones((2, 2, 4)))
+    yd = torch.empty_like(xd)
+    with pytest.raises(attn.AttnError) as e:
+        attn.attn_heff_apply(H, xd, yd, attn.ATTN_BF16)
+    assert e.value.status == 8
+    attn.attn_heff_destroy(H)
+    attn.attn_destroy(ctx)
+
+
+def test_mixed_precision_eigsolve_is_fp64_accurate():
+    """BF16 Lanczos followed by FP64 refinement on a physical H_eff (8x8 TFIM, m = 32,
+    top node): the returned value is the FP64 Rayleigh quotient of the returned vector,
+    it is variational (>= the converged FP64 eigenvalue) and the refinement lowers the
+    FP64 residual of the BF16 Ritz pair (Sec. 4.4.2 with the mixed-precision policy)."""
+    from inputs import raw_tree_tensors
+    from oracle.tree import Tree
+
+    attn, ctx = lib_and_ctx()
+    tree = Tree(64, 32)
+    model = attn.attn_model_tfim(ctx, 8, 3.04)
+    st = attn.attn_state_create(ctx, model, 32, raw_tree_tensors(tree.shape, 0))
+    attn.attn_de_place(st, 16)
+    attn.attn_map_hamiltonian(st)
+    attn.attn_ttn_sweep(st)  # a physical state
+    node = tree.top_nodes()[0]
+    attn.attn_move_centre(st, node)
+    H = attn.attn_heff_build(st, node)
+    x0 = attn.attn_node_get(st, node)
+    cfg = attn.attn_get_config(ctx)
+    cfg.lanczos_depth = 60
+    cfg.lanczos_tol = 1e-14
+    cfg.matvec_dtype = attn.ATTN_F64
+    attn.attn_set_config(ctx, cfg)
+    t64 = dev(x0)
+    th64, _ = attn.attn_eigsolve(H, t64)
+    import torch
+
+    def rq_and_res(vd):
+        w = torch.empty_like(vd)
+        attn.attn_heff_apply(H, vd, w, attn.ATTN_F64)
+        th = float(torch.dot(vd.reshape(-1), w.reshape(-1)) / torch.dot(vd.reshape(-1), vd.reshape(-1)))
+        return th, float(torch.linalg.norm(w - th * vd))
+
+    cfg.lanczos_depth = 20
+    cfg.matvec_dtype = attn.ATTN_BF16
+    cfg.refine_steps = 0
+    attn.attn_set_config(ctx, cfg)
+    tlo = dev(x0)
+    attn.attn_eigsolve(H, tlo)
+    _, res_lo = rq_and_res(tlo)
+    cfg.refine_steps = 8
+    cfg.refine_tol = 1e-13
+    attn.attn_set_config(ctx, cfg)
+    tmx = dev(x0)
+    thmx, _ = attn.attn_eigsolve(H, tmx)
+    rq, res_mx = rq_and_res(tmx)
+    assert abs(thmx - rq) < 1e-12 * abs(rq)
+    assert thmx >= th64 - 1e-9 * abs(th64)
+    assert res_mx < 0.5 * res_lo
+    attn.attn_heff_destroy(H)
+    attn.attn_state_destroy(st)
+    attn.attn_model_destroy(model)
+    attn.attn_destroy(ctx)
