@@ -82,7 +82,8 @@ typedef struct {
   attn_dtype matvec_dtype;  /* precision of the H_eff contractions in Lanczos (ATTN_F64) */
   int refine_steps;         /* FP64 residual-correction steps after a low-precision Lanczos (3) */
   double refine_tol;        /* stop refining when ||H v - theta v|| < tol |theta| (1e-10) */
-  int reserved[8];
+  int use_graphs;           /* attn_eigsolve replays a captured CUDA graph of the whole solve (0) */
+  int reserved[7];
 } attn_config;
 
 ATTN_API attn_status attn_config_default(attn_config* cfg);
@@ -96,8 +97,9 @@ ATTN_API const char* attn_version(void);
 /* ----------------------------------------------------------------- context */
 
 /* Create a context on the current CUDA device. cuda_stream is a cudaStream_t
- * (NULL: the library creates its own non-blocking stream). cfg may be NULL
- * (defaults). */
+ * on which all of the context's work is enqueued (NULL: the legacy default
+ * stream, which is also what PyTorch's default stream reports). cfg may be
+ * NULL (defaults). */
 ATTN_API attn_status attn_create(const attn_config* cfg, void* cuda_stream, attn_ctx** out);
 ATTN_API attn_status attn_destroy(attn_ctx* ctx);
 ATTN_API attn_status attn_set_config(attn_ctx* ctx, const attn_config* cfg);
@@ -106,6 +108,15 @@ ATTN_API attn_status attn_get_config(attn_ctx* ctx, attn_config* cfg);
 ATTN_API attn_status attn_sync(attn_ctx* ctx);
 /* Number of library kernels launched by this context so far. */
 ATTN_API attn_status attn_kernel_launches(attn_ctx* ctx, uint64_t* count);
+/* Kernel timing for measurement tools. enable != 0 clears the records and
+ * makes the library bracket each launch of its main kernels with a CUDA event
+ * pair on the context stream: kernel_id 0 = tensor-core H_eff kernel,
+ * 1 = FP64 contraction kernel, 2 = tensor-core GEMM kernel. attn_profile_read
+ * waits for the last recorded event and returns the summed device time (ms),
+ * the number of recorded launches and their algorithmic FLOPs (Sec. 4.4.2
+ * counting: 2 m_l V per operator applied on link l of a tensor of V entries). */
+ATTN_API attn_status attn_profile_enable(attn_ctx* ctx, int enable);
+ATTN_API attn_status attn_profile_read(attn_ctx* ctx, int kernel_id, double* total_ms, int* launches, double* flops);
 
 /* ------------------------------------------------------------------ models */
 
@@ -230,6 +241,24 @@ ATTN_API attn_status attn_local_step(attn_state* st, int node, double* energy);
 ATTN_API attn_status attn_ttn_sweep(attn_state* st, double* energy);
 /* Energy <T|H_eff|T> at the centre (FP64). */
 ATTN_API attn_status attn_energy(attn_state* st, double* energy);
+
+/* MERA-like update of every placed disentangler for the current TTN
+ * (Sec. 4.1.1, Eqs. contracted and cost function): the environments (the
+ * TTN's reduced density matrices on each disentangler's terms, Sec. 4.2) are
+ * contracted once on the GPU; then, per disentangler, Gamma_k with u^T fixed,
+ * u = -V W^T from the SVD Gamma_k = W sigma V^T, accepted while the true E_k
+ * does not increase, up to de_max_iter steps or a relative change below
+ * de_rel_dev. Terms are shifted by their spectral norm (reading: the paper
+ * gives no shift). All disentanglers are independent given the TTN
+ * (restriction 1) and are updated in one batch. *dE (may be NULL) receives
+ * sum_k [E_k(new) - E_k(old)]. The mapped Hamiltonian is marked stale. */
+ATTN_API attn_status attn_de_update(attn_state* st, double* dE);
+/* E_k before and after the last attn_de_update, 2 doubles per disentangler. */
+ATTN_API attn_status attn_de_energies(attn_state* st, double* e_out);
+/* One aTTN sweep (Sec. 4): if s_ttn sweeps have been done and disentanglers
+ * are placed, update all disentanglers; map H -> H' if needed; then one TTN
+ * sweep under H'. *energy receives the last local energy (= E of the state). */
+ATTN_API attn_status attn_sweep(attn_state* st, double* energy);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,7 @@ class attn_config(ctypes.Structure):
                 ("de_max_iter", ctypes.c_int), ("de_rel_dev", ctypes.c_double),
                 ("s_ttn", ctypes.c_int), ("matvec_dtype", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("refine_tol", ctypes.c_double),
-                ("reserved", ctypes.c_int * 8)]
+                ("use_graphs", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class attn_heff_desc(ctypes.Structure):
@@ -54,6 +54,8 @@ _SIGS = {
     "attn_get_config": [_P, ctypes.POINTER(attn_config)],
     "attn_sync": [_P],
     "attn_kernel_launches": [_P, ctypes.POINTER(ctypes.c_uint64)],
+    "attn_profile_enable": [_P, _I],
+    "attn_profile_read": [_P, _I, _PD, _PI, _PD],
     "attn_model_tfim": [_P, _I, _D, _PP],
     "attn_model_tri_heisenberg": [_P, _I, _D, _PP],
     "attn_model_terms": [_P, _I, _I, _PI, _PI, _PD, _PP],
@@ -86,6 +88,9 @@ _SIGS = {
     "attn_local_step": [_P, _I, _PD],
     "attn_ttn_sweep": [_P, _PD],
     "attn_energy": [_P, _PD],
+    "attn_de_update": [_P, _PD],
+    "attn_de_energies": [_P, _PD],
+    "attn_sweep": [_P, _PD],
 }
 
 _lib = None
@@ -184,6 +189,17 @@ def attn_kernel_launches(ctx):
     c = ctypes.c_uint64()
     _check(load().attn_kernel_launches(ctx, ctypes.byref(c)))
     return c.value
+
+
+def attn_profile_enable(ctx, enable=True):
+    _check(load().attn_profile_enable(ctx, 1 if enable else 0))
+
+
+def attn_profile_read(ctx, kernel_id):
+    """(total device ms, launches, algorithmic FLOPs) of the recorded launches."""
+    ms, n, fl = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+    _check(load().attn_profile_read(ctx, kernel_id, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)))
+    return ms.value, n.value, fl.value
 
 
 # ---------------------------------------------------------------------- models
@@ -399,4 +415,23 @@ def attn_ttn_sweep(st):
 def attn_energy(st):
     e = ctypes.c_double()
     _check(load().attn_energy(st, ctypes.byref(e)))
+    return e.value
+
+
+# ------------------------------------------------------------ disentangler update
+def attn_de_update(st):
+    d = ctypes.c_double()
+    _check(load().attn_de_update(st, ctypes.byref(d)))
+    return d.value
+
+
+def attn_de_energies(st, n_de):
+    out = np.zeros(2 * max(n_de, 1))
+    _check(load().attn_de_energies(st, out.ctypes.data_as(_PD)))
+    return out[:2 * n_de].reshape(n_de, 2)
+
+
+def attn_sweep(st):
+    e = ctypes.c_double()
+    _check(load().attn_sweep(st, ctypes.byref(e)))
     return e.value

@@ -69,6 +69,28 @@ struct attn_ctx {
   attn::DevBuf ws[4];
   attn::DevBuf scal;      // small device scalars
   attn::DevBuf partials;  // reduction partials (fixed size, allocated at creation)
+  // Optional per-kernel timing (attn_profile_enable): event pairs around launches.
+  bool prof_on = false;
+  struct ProfRec {
+    std::vector<cudaEvent_t> ev;  // start/stop interleaved
+    size_t used = 0;              // events in use (pairs * 2)
+    double flops = 0.0;           // algorithmic FLOPs of the recorded launches
+    int launches = 0;
+    double acc_ms = 0.0;          // harvested from graph replays
+    double acc_flops = 0.0;
+    int acc_launches = 0;
+  } prof[4];
+  // While a CUDA graph is being captured, launch events go to this list
+  // (kernel id, start, stop, FLOPs) instead of the pool above.
+  struct GraphEv {
+    int kid;
+    cudaEvent_t a, b;
+    double flops;
+  };
+  std::vector<GraphEv>* capture_events = nullptr;
+  void prof_begin(int kid);
+  void prof_end(int kid, double flops);
+  ~attn_ctx();
 };
 
 namespace attn {

@@ -47,6 +47,47 @@ void DevBuf::reserve(size_t n) {
 
 }  // namespace attn
 
+void attn_ctx::prof_begin(int kid) {
+  if (!prof_on) return;
+  if (capture_events) {
+    GraphEv g{kid, nullptr, nullptr, 0.0};
+    ATTN_CHECK_CUDA(cudaEventCreate(&g.a));
+    ATTN_CHECK_CUDA(cudaEventCreate(&g.b));
+    ATTN_CHECK_CUDA(cudaEventRecord(g.a, stream));
+    capture_events->push_back(g);
+    return;
+  }
+  ProfRec& p = prof[kid];
+  if (p.used + 2 > p.ev.size()) {
+    cudaEvent_t a, b;
+    ATTN_CHECK_CUDA(cudaEventCreate(&a));
+    ATTN_CHECK_CUDA(cudaEventCreate(&b));
+    p.ev.push_back(a);
+    p.ev.push_back(b);
+  }
+  ATTN_CHECK_CUDA(cudaEventRecord(p.ev[p.used], stream));
+}
+
+void attn_ctx::prof_end(int kid, double flops) {
+  if (!prof_on) return;
+  if (capture_events) {
+    GraphEv& g = capture_events->back();
+    ATTN_CHECK_CUDA(cudaEventRecord(g.b, stream));
+    g.flops = flops;
+    return;
+  }
+  ProfRec& p = prof[kid];
+  ATTN_CHECK_CUDA(cudaEventRecord(p.ev[p.used + 1], stream));
+  p.used += 2;
+  p.flops += flops;
+  p.launches += 1;
+}
+
+attn_ctx::~attn_ctx() {
+  for (auto& p : prof)
+    for (auto e : p.ev) cudaEventDestroy(e);
+}
+
 using namespace attn;
 
 #define ATTN_TRY try {
@@ -112,12 +153,9 @@ ATTN_API attn_status attn_create(const attn_config* cfg, void* stream, attn_ctx*
   ATTN_REQUIRE(prop.major == 10 && prop.minor == 3, ATTN_ECUDA,
                std::string("libattn is built for sm_103a only; device is ") + prop.name);
   ctx->num_sms = prop.multiProcessorCount;
-  if (stream) {
-    ctx->stream = (cudaStream_t)stream;
-  } else {
-    ATTN_CHECK_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
-    ctx->own_stream = true;
-  }
+  // NULL selects the legacy default stream (what torch's default stream reports as 0)
+  ctx->stream = stream ? (cudaStream_t)stream : (cudaStream_t)0;
+  ctx->own_stream = false;
   ctx->partials.reserve(sizeof(double) * 512 * 64);
   ctx->scal.reserve(sizeof(double) * 64);
   *out = ctx.release();
@@ -156,6 +194,38 @@ ATTN_API attn_status attn_sync(attn_ctx* ctx) {
   ATTN_TRY
   NEED(ctx, "ctx");
   ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_profile_enable(attn_ctx* ctx, int enable) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  ctx->prof_on = enable != 0;
+  for (auto& p : ctx->prof) {
+    p.used = 0;
+    p.flops = 0.0;
+    p.launches = 0;
+    p.acc_ms = p.acc_flops = 0.0;
+    p.acc_launches = 0;
+  }
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_profile_read(attn_ctx* ctx, int kernel_id, double* total_ms, int* launches, double* flops) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  ATTN_REQUIRE(kernel_id >= 0 && kernel_id < 4, ATTN_EINVAL, "kernel_id must be 0..3");
+  attn_ctx::ProfRec& p = ctx->prof[kernel_id];
+  double tot = 0.0;
+  if (p.used) ATTN_CHECK_CUDA(cudaEventSynchronize(p.ev[p.used - 1]));
+  for (size_t i = 0; i + 1 < p.used; i += 2) {
+    float ms = 0.f;
+    ATTN_CHECK_CUDA(cudaEventElapsedTime(&ms, p.ev[i], p.ev[i + 1]));
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot + p.acc_ms;
+  if (launches) *launches = p.launches + p.acc_launches;
+  if (flops) *flops = p.flops + p.acc_flops;
   ATTN_CATCH
 }
 
@@ -531,12 +601,78 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
   NEED(theta, "theta");
   attn_ctx* ctx = h->ctx;
   const attn_config& cfg = ctx->cfg;
-  LanczosWork w;
   const attn_dtype dt = cfg.matvec_dtype;
   MatVec lo = [&](const double* a, double* b) {
     if (dt == ATTN_BF16) h->apply_bf16(a, b); else h->apply_f64(a, b);
   };
   MatVec hi = [&](const double* a, double* b) { h->apply_f64(a, b); };
+  const int rsteps = (dt != ATTN_F64) ? cfg.refine_steps : 0;
+  if (cfg.use_graphs) {
+    EigGraph* g = h->eg;
+    if (!g || g->x != T_dev || g->depth != cfg.lanczos_depth || g->tol != cfg.lanczos_tol || g->dtype != dt ||
+        g->refine != rsteps || g->rtol != cfg.refine_tol || g->prof != ctx->prof_on) {
+      delete g;
+      g = h->eg = new EigGraph();
+      g->x = T_dev;
+      g->depth = cfg.lanczos_depth;
+      g->tol = cfg.lanczos_tol;
+      g->dtype = dt;
+      g->refine = rsteps;
+      g->rtol = cfg.refine_tol;
+      g->prof = ctx->prof_on;
+      // warm-up on a scratch copy: every buffer the solve needs is allocated before capture
+      ctx->ws[3].reserve(sizeof(double) * h->V);
+      copy_f64(ctx, ctx->ws[3].as<double>(), T_dev, h->V);
+      const bool prof_was = ctx->prof_on;
+      ctx->prof_on = false;
+      lanczos_enqueue(ctx, lo, ctx->ws[3].as<double>(), h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0);
+      if (rsteps > 0) lanczos_enqueue(ctx, hi, ctx->ws[3].as<double>(), h->V, rsteps + 1, cfg.refine_tol, g->w, 0);
+      ctx->prof_on = prof_was;
+      ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+      cudaStream_t user = ctx->stream, cs;
+      ATTN_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      const uint64_t l0 = ctx->launches;
+      ctx->stream = cs;
+      ctx->capture_events = &g->evs;
+      cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+      try {
+        ATTN_CHECK_CUDA(ce);
+        lanczos_enqueue(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0);
+        if (rsteps > 0) lanczos_enqueue(ctx, hi, T_dev, h->V, rsteps + 1, cfg.refine_tol, g->w, 0);
+      } catch (...) {
+        cudaGraph_t tmp = nullptr;
+        cudaStreamEndCapture(cs, &tmp);
+        if (tmp) cudaGraphDestroy(tmp);
+        ctx->stream = user;
+        ctx->capture_events = nullptr;
+        cudaStreamDestroy(cs);
+        delete g;
+        h->eg = nullptr;
+        throw;
+      }
+      ATTN_CHECK_CUDA(cudaStreamEndCapture(cs, &g->graph));
+      ctx->stream = user;
+      ctx->capture_events = nullptr;
+      ATTN_CHECK_CUDA(cudaStreamDestroy(cs));
+      g->launches = ctx->launches - l0;
+      ctx->launches = l0;
+      ATTN_CHECK_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
+    }
+    ATTN_CHECK_CUDA(cudaGraphLaunch(g->exec, ctx->stream));
+    ctx->launches += g->launches;
+    LanczosResult r = lanczos_read(ctx, g->w);
+    for (auto& e : g->evs) {
+      float ms = 0.f;
+      ATTN_CHECK_CUDA(cudaEventElapsedTime(&ms, e.a, e.b));
+      ctx->prof[e.kid].acc_ms += ms;
+      ctx->prof[e.kid].acc_flops += e.flops;
+      ctx->prof[e.kid].acc_launches += 1;
+    }
+    *theta = r.theta;
+    if (iters) *iters = r.iters;
+    return ATTN_OK;
+  }
+  LanczosWork w;
   LanczosResult r = lanczos_lowest(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, w);
   int it = r.iters;
   if (dt != ATTN_F64 && cfg.refine_steps > 0) {
@@ -565,6 +701,36 @@ ATTN_API attn_status attn_ttn_sweep(attn_state* st, double* energy) {
   double e = 0;
   for (int n : st->tree.post_order()) e = st->local_step(n);
   ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  if (energy) *energy = e;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_de_update(attn_state* st, double* dE) {
+  ATTN_TRY
+  NEED(st, "state");
+  double d = st->de_update(nullptr, nullptr);
+  if (dE) *dE = d;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_de_energies(attn_state* st, double* e_out) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(e_out, "e_out");
+  std::copy(st->last_de_energy.begin(), st->last_de_energy.end(), e_out);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_sweep(attn_state* st, double* energy) {
+  ATTN_TRY
+  NEED(st, "state");
+  const attn_config& cfg = st->ctx->cfg;
+  if (st->sweep_count >= cfg.s_ttn && !st->des.empty()) st->de_update(nullptr, nullptr);
+  if (!st->mapped_ready) st->set_products();
+  double e = 0;
+  for (int n : st->tree.post_order()) e = st->local_step(n);
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  st->sweep_count++;
   if (energy) *energy = e;
   ATTN_CATCH
 }

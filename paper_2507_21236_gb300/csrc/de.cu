@@ -1,0 +1,616 @@
+// Disentangler update on the GPU (Sec. 4.1: Eqs. energy, contracted, cost
+// function; Sec. 4.2: environments of a disentangler).
+//
+// With restriction (1) the energy splits as E = sum_k E_k(u_k) + const. For a
+// disentangler u on sites (i, j) and an original term h_p touching i or j:
+//  - if h_p lives on {i, j} only, with C_p its 4x4 form on (i, j):
+//        E_p(u) = Tr(rho_ij u^T C_p u);
+//  - if h_p also touches a third site e, write h_p = sum_r C_r (x) f_r across
+//    (ij)|e (exact SVD split, r <= 4) and M_r = Tr_e[rho_ije (1 (x) f_r)]:
+//        E_p(u) = sum_r Tr(M_r u^T C_r u).
+// Fixing the transposed factor at u_old makes the energy linear in u,
+// E = Tr(u Gamma) (Eq. contracted) with
+//        Gamma = sum_p sum_r M_r u_old^T C_r - (sum_p lambda_p) rho_ij u_old^T,
+// where every term is shifted by lambda_p = ||h_p||_2 (negative semidefinite
+// h~_p; a u-independent constant). The minimiser is u = -V W^T for
+// Gamma = W sigma V^T (Eq. cost function); steps are accepted while the true
+// E_k does not increase, at most de_max_iter of them, stopping when the
+// relative change falls below de_rel_dev.
+//
+// rho_ij and the M_r are expectation values of products of one-site factors
+// (matrix units on i and j, f_r on e). They are computed by renormalising the
+// factors from their sites to the isometry centre along the tree (the path
+// contraction of Sec. 4.2.1 for all disentanglers at once, with identical
+// partial products shared), then contracting with the centre tensor. The
+// 4x4 iterations of all disentanglers run in one kernel, one thread each,
+// with a one-sided Jacobi SVD.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <set>
+
+#include "lanczos.h"
+#include "state.h"
+
+using namespace attn;
+
+namespace attn {
+
+// mode product and contraction helpers from state.cu / gemm_f64.cu
+void gather_rows_f64(attn_ctx* ctx, double* dst, const double* src, const int* idx_dev, int R, long len);
+
+namespace {
+
+constexpr int kMaxEnt = 48;  // entries per disentangler handled by the kernel
+
+__device__ void mm4(const double* a, const double* b, double* c) {  // c = a b
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0;
+      for (int q = 0; q < 4; ++q) s += a[i * 4 + q] * b[q * 4 + j];
+      c[i * 4 + j] = s;
+    }
+}
+__device__ void mtm4(const double* a, const double* b, double* c) {  // c = a^T b
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0;
+      for (int q = 0; q < 4; ++q) s += a[q * 4 + i] * b[q * 4 + j];
+      c[i * 4 + j] = s;
+    }
+}
+
+struct DEArgs {
+  int n_de;
+  const int* ent_begin;   // [n_de + 1]
+  const int* ent_midx;    // [n_ent][16] indices into vals (M[a][b])
+  const double* ent_C;    // [n_ent][16]
+  const double* lambda;   // [n_de]
+  const int* rho_idx;     // [n_de][16]
+  const double* vals;     // probe expectation values
+  const double* u_in;     // [n_de][16]
+  double* u_out;          // [n_de][16]
+  double* e_out;          // [n_de][2]: E_k(u_in), E_k(u_out)
+  int max_iter;
+  double rel_dev;
+};
+
+__device__ double de_energy(const DEArgs& a, int b0, int b1, const double* u) {
+  double e = 0.0;
+  double uc[16], w[16];
+  for (int q = b0; q < b1; ++q) {
+    const double* C = a.ent_C + 16L * q;
+    mm4(C, u, w);      // C u
+    mtm4(u, w, uc);    // u^T C u
+    for (int al = 0; al < 4; ++al)
+      for (int be = 0; be < 4; ++be) e += a.vals[a.ent_midx[16L * q + al * 4 + be]] * uc[be * 4 + al];
+  }
+  return e;
+}
+
+__device__ void de_gamma(const DEArgs& a, int k, int b0, int b1, const double* u, double* g) {
+  double M[16], utc[16], t[16];
+  for (int i = 0; i < 16; ++i) g[i] = 0.0;
+  for (int q = b0; q < b1; ++q) {
+    const double* C = a.ent_C + 16L * q;
+    for (int i = 0; i < 16; ++i) M[i] = a.vals[a.ent_midx[16L * q + i]];
+    mtm4(u, C, utc);  // u^T C
+    mm4(M, utc, t);
+    for (int i = 0; i < 16; ++i) g[i] += t[i];
+  }
+  double rho[16], ut[16];
+  for (int i = 0; i < 16; ++i) rho[i] = a.vals[a.rho_idx[16L * k + i]];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) ut[i * 4 + j] = u[j * 4 + i];
+  mm4(rho, ut, t);
+  for (int i = 0; i < 16; ++i) g[i] -= a.lambda[k] * t[i];
+}
+
+// u = -V W^T for G = W diag(s) V^T (one-sided Jacobi on the columns of G).
+__device__ void mera_solve(const double* G, double* u) {
+  double B[16], J[16];
+  for (int i = 0; i < 16; ++i) { B[i] = G[i]; J[i] = (i % 5 == 0) ? 1.0 : 0.0; }
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < 4; ++p)
+      for (int q = p + 1; q < 4; ++q) {
+        double a = 0, b = 0, c = 0;
+        for (int r = 0; r < 4; ++r) {
+          a += B[r * 4 + p] * B[r * 4 + p];
+          b += B[r * 4 + q] * B[r * 4 + q];
+          c += B[r * 4 + p] * B[r * 4 + q];
+        }
+        if (c == 0.0 || a == 0.0 || b == 0.0) continue;
+        double ratio = fabs(c) / sqrt(a * b);
+        if (!(ratio > 1e-16)) continue;
+        off = fmax(off, ratio);
+        double zeta = (b - a) / (2.0 * c);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        for (int r = 0; r < 4; ++r) {
+          double x = B[r * 4 + p], y = B[r * 4 + q];
+          B[r * 4 + p] = cs * x - sn * y;
+          B[r * 4 + q] = sn * x + cs * y;
+          x = J[r * 4 + p];
+          y = J[r * 4 + q];
+          J[r * 4 + p] = cs * x - sn * y;
+          J[r * 4 + q] = sn * x + cs * y;
+        }
+      }
+    if (off < 1e-15) break;
+  }
+  double W[16], s[4], smax = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    double n = 0;
+    for (int r = 0; r < 4; ++r) n += B[r * 4 + k] * B[r * 4 + k];
+    s[k] = sqrt(n);
+    smax = fmax(smax, s[k]);
+  }
+  bool done[4];
+  for (int k = 0; k < 4; ++k) {
+    done[k] = s[k] > 1e-13 * smax && s[k] > 0.0;
+    for (int r = 0; r < 4; ++r) W[r * 4 + k] = done[k] ? B[r * 4 + k] / s[k] : 0.0;
+  }
+  // complete rank-deficient columns with unit vectors orthogonalised against the others
+  for (int k = 0; k < 4; ++k) {
+    if (done[k]) continue;
+    for (int tr = 0; tr < 4; ++tr) {
+      double v[4] = {0, 0, 0, 0};
+      v[tr] = 1.0;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int o = 0; o < 4; ++o) {
+          if (!done[o]) continue;
+          double d = 0;
+          for (int r = 0; r < 4; ++r) d += W[r * 4 + o] * v[r];
+          for (int r = 0; r < 4; ++r) v[r] -= d * W[r * 4 + o];
+        }
+      double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3]);
+      if (n > 0.5) {
+        for (int r = 0; r < 4; ++r) W[r * 4 + k] = v[r] / n;
+        done[k] = true;
+        break;
+      }
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double acc = 0;
+      for (int q = 0; q < 4; ++q) acc += J[i * 4 + q] * W[j * 4 + q];
+      u[i * 4 + j] = -acc;
+    }
+}
+
+__global__ void de_mera_kernel(DEArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.n_de) return;
+  const int b0 = a.ent_begin[k], b1 = a.ent_begin[k + 1];
+  double u[16], g[16], un[16];
+  for (int i = 0; i < 16; ++i) u[i] = a.u_in[16L * k + i];
+  double e = de_energy(a, b0, b1, u);
+  a.e_out[2 * k] = e;
+  for (int it = 0; it < a.max_iter; ++it) {
+    de_gamma(a, k, b0, b1, u, g);
+    mera_solve(g, un);
+    const double en = de_energy(a, b0, b1, un);
+    if (!(en <= e + 1e-14 * fmax(1.0, fabs(e)))) break;
+    const bool done = fabs(en - e) <= a.rel_dev * fmax(fabs(e), 1e-300);
+    for (int i = 0; i < 16; ++i) u[i] = un[i];
+    e = en;
+    if (done) break;
+  }
+  for (int i = 0; i < 16; ++i) a.u_out[16L * k + i] = u[i];
+  a.e_out[2 * k + 1] = e;
+}
+
+__global__ void scale_vals(double* v, int n, const double* nrm_sq) {
+  const double inv = 1.0 / *nrm_sq;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] *= inv;
+}
+
+void upload(attn_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
+  b.reserve(std::max<size_t>(bytes, 16));
+  if (bytes) ATTN_CHECK_CUDA(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+}
+
+// Embed an operator on `sites` (ascending) into the ordered site list `target` (any order).
+std::vector<double> embed_any(const std::vector<double>& op, const std::vector<int>& sites,
+                              const std::vector<int>& target) {
+  const int k = (int)sites.size(), kt = (int)target.size(), D = 1 << kt;
+  std::vector<int> pos(k);
+  for (int a = 0; a < k; ++a) pos[a] = (int)(std::find(target.begin(), target.end(), sites[a]) - target.begin());
+  std::vector<double> out((size_t)D * D, 0.0);
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) {
+      bool same = true;
+      int ri = 0, ci = 0;
+      for (int b = 0; b < kt; ++b) {
+        const int rb = (r >> (kt - 1 - b)) & 1, cb = (c >> (kt - 1 - b)) & 1;
+        int a = -1;
+        for (int q = 0; q < k; ++q)
+          if (pos[q] == b) a = q;
+        if (a < 0) {
+          if (rb != cb) same = false;
+        } else {
+          ri |= rb << (k - 1 - a);
+          ci |= cb << (k - 1 - a);
+        }
+      }
+      if (same) out[(size_t)r * D + c] = op[(size_t)ri * (1 << k) + ci];
+    }
+  return out;
+}
+
+// Singular triplets of a small dense matrix (rows x cols, row-major) by one-sided Jacobi.
+void small_svd(const std::vector<double>& A, int rows, int cols, std::vector<double>& U, std::vector<double>& s,
+               std::vector<double>& V) {
+  // B = A (rows x cols); rotate columns
+  std::vector<double> B = A;
+  V.assign((size_t)cols * cols, 0.0);
+  for (int i = 0; i < cols; ++i) V[i * cols + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < cols; ++p)
+      for (int q = p + 1; q < cols; ++q) {
+        double a = 0, b = 0, c = 0;
+        for (int r = 0; r < rows; ++r) {
+          a += B[r * cols + p] * B[r * cols + p];
+          b += B[r * cols + q] * B[r * cols + q];
+          c += B[r * cols + p] * B[r * cols + q];
+        }
+        if (c == 0.0 || a == 0.0 || b == 0.0) continue;
+        double ratio = std::fabs(c) / std::sqrt(a * b);
+        if (!(ratio > 1e-16)) continue;
+        off = std::max(off, ratio);
+        double zeta = (b - a) / (2.0 * c);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / std::sqrt(1.0 + t * t), sn = cs * t;
+        for (int r = 0; r < rows; ++r) {
+          double x = B[r * cols + p], y = B[r * cols + q];
+          B[r * cols + p] = cs * x - sn * y;
+          B[r * cols + q] = sn * x + cs * y;
+        }
+        for (int r = 0; r < cols; ++r) {
+          double x = V[r * cols + p], y = V[r * cols + q];
+          V[r * cols + p] = cs * x - sn * y;
+          V[r * cols + q] = sn * x + cs * y;
+        }
+      }
+    if (off < 1e-15) break;
+  }
+  s.assign(cols, 0.0);
+  U.assign((size_t)rows * cols, 0.0);
+  for (int k = 0; k < cols; ++k) {
+    double n = 0;
+    for (int r = 0; r < rows; ++r) n += B[r * cols + k] * B[r * cols + k];
+    s[k] = std::sqrt(n);
+    for (int r = 0; r < rows; ++r) U[r * cols + k] = s[k] > 0 ? B[r * cols + k] / s[k] : 0.0;
+  }
+}
+
+}  // namespace
+}  // namespace attn
+
+// ----------------------------------------------------- probe expectations
+void attn_state::probe_expectations(const std::vector<ProbeFactor>& F, const std::vector<Probe>& P, DevBuf& vals) {
+  using Key = std::vector<int>;
+  const int c0 = centre;
+  const int NP = (int)P.size();
+  auto slot_of = [&](int n, int site) {
+    for (int s = 0; s < 3; ++s)
+      if (tree.behind(n, s, site)) return s;
+    throw Error{ATTN_EINVAL, "site not behind any link"};
+  };
+  std::vector<std::array<Key, 3>> pk(NP);
+  std::map<int, std::set<Key>> need;
+  for (int q = 0; q < NP; ++q) {
+    for (int a = 0; a < P[q].n; ++a) pk[q][slot_of(c0, F[P[q].f[a]].site)].push_back(P[q].f[a]);
+    for (int s = 0; s < 3; ++s) {
+      std::sort(pk[q][s].begin(), pk[q][s].end());
+      if (!pk[q][s].empty()) need[3 * c0 + s].insert(pk[q][s]);
+    }
+  }
+  std::vector<int> order;
+  std::vector<int> queue;
+  for (int s = 0; s < 3; ++s)
+    if (need.count(3 * c0 + s)) queue.push_back(3 * c0 + s);
+  std::set<int> seen(queue.begin(), queue.end());
+  for (size_t qi = 0; qi < queue.size(); ++qi) {
+    const int L = queue[qi];
+    order.push_back(L);
+    const Tree::Nbr& nb = tree.nbr[L];
+    if (nb.kind == 0) continue;
+    const int c = nb.idx, t = nb.back;
+    int xs[2], ni = 0;
+    for (int s = 0; s < 3; ++s)
+      if (s != t) xs[ni++] = s;
+    for (const Key& K : need[L]) {
+      // kx holds the factors behind c's slot xs[0], ky those behind xs[1]
+      Key kx, ky;
+      for (int f : K) {
+        const int s = slot_of(c, F[f].site);
+        ATTN_REQUIRE(s != t, ATTN_EINVAL, "probe bookkeeping error");
+        (s == xs[0] ? kx : ky).push_back(f);
+      }
+      if (!kx.empty()) need[3 * c + xs[0]].insert(kx);
+      if (!ky.empty()) need[3 * c + xs[1]].insert(ky);
+    }
+    for (int s = 0; s < 3; ++s) {
+      if (s == t) continue;
+      const int L2 = 3 * c + s;
+      if (need.count(L2) && !seen.count(L2)) {
+        seen.insert(L2);
+        queue.push_back(L2);
+      }
+    }
+  }
+  struct PL {
+    std::vector<Key> keys;
+    std::map<Key, int> idx;
+    DevBuf ops;
+  };
+  std::map<int, PL> pl;
+  for (auto it = order.rbegin(); it != order.rend(); ++it) {
+    const int L = *it;
+    const int n = L / 3, slot = L % 3;
+    PL& o = pl[L];
+    const Tree::Nbr& nb = tree.nbr[L];
+    const int dimL = dim(n, slot);
+    const long osz = (long)dimL * dimL;
+    if (nb.kind == 0) {
+      std::vector<double> h;
+      for (const Key& K : need[L]) {
+        ATTN_REQUIRE(K.size() == 1 && F[K[0]].site == nb.idx, ATTN_EINVAL, "probe bookkeeping error (site)");
+        o.idx[K] = (int)o.keys.size();
+        o.keys.push_back(K);
+        h.insert(h.end(), F[K[0]].op, F[K[0]].op + 4);
+      }
+      upload(ctx, o.ops, h.data(), sizeof(double) * h.size());
+      continue;
+    }
+    const int c = nb.idx, t = nb.back;
+    int xs[2], ni = 0;
+    for (int s = 0; s < 3; ++s)
+      if (s != t) xs[ni++] = s;
+    const PL& Px = pl[3 * c + xs[0]];
+    const PL& Py = pl[3 * c + xs[1]];
+    std::vector<Key> gb, gx, gy;
+    std::vector<int> bx, by, xi, yi;
+    for (const Key& K : need[L]) {
+      Key kx, ky;
+      for (int f : K) (slot_of(c, F[f].site) == xs[0] ? kx : ky).push_back(f);
+      if (!kx.empty() && !ky.empty()) {
+        gb.push_back(K);
+        bx.push_back(Px.idx.at(kx));
+        by.push_back(Py.idx.at(ky));
+      } else if (!kx.empty()) {
+        gx.push_back(K);
+        xi.push_back(Px.idx.at(kx));
+      } else {
+        gy.push_back(K);
+        yi.push_back(Py.idx.at(ky));
+      }
+    }
+    for (auto* g : {&gb, &gx, &gy})
+      for (const Key& K : *g) {
+        o.idx[K] = (int)o.keys.size();
+        o.keys.push_back(K);
+      }
+    o.ops.reserve(sizeof(double) * std::max<size_t>(1, o.keys.size()) * osz);
+    const int d[3] = {dim(c, 0), dim(c, 1), dim(c, 2)};
+    const double* Tc = tensor(c);
+    const double* Ax = Px.ops.as<double>();
+    const double* By = Py.ops.as<double>();
+    double* out = o.ops.as<double>();
+    if (!gb.empty()) renorm_batch(Tc, d, t, xs[0], xs[1], Ax, bx, By, by, out);
+    if (!gx.empty()) renorm_batch(Tc, d, t, xs[0], xs[1], Ax, xi, nullptr, {}, out + (long)gb.size() * osz);
+    if (!gy.empty())
+      renorm_batch(Tc, d, t, xs[0], xs[1], nullptr, {}, By, yi, out + (long)(gb.size() + gx.size()) * osz);
+  }
+  // contract at the centre: <T| (x)_s O_s |T> / <T|T>, grouped by slot pattern
+  const int d[3] = {dim(c0, 0), dim(c0, 1), dim(c0, 2)};
+  const long V = vol(c0);
+  vals.reserve(sizeof(double) * std::max(NP, 1) + 64);
+  double* dv = vals.as<double>();
+  std::vector<std::vector<int>> by_pat(8);
+  for (int q = 0; q < NP; ++q) {
+    int mask = 0;
+    for (int s = 0; s < 3; ++s)
+      if (!pk[q][s].empty()) mask |= 1 << s;
+    by_pat[mask].push_back(q);
+  }
+  std::vector<int> pos(NP, -1);
+  int filled = 0;
+  const long budget = 1L << 26;
+  const int chunk = (int)std::max<long>(1, std::min<long>(512, budget / std::max<long>(V, 1)));
+  std::vector<int> out_order;
+  for (int mask = 1; mask < 8; ++mask) {
+    const std::vector<int>& qs = by_pat[mask];
+    for (size_t r0 = 0; r0 < qs.size(); r0 += chunk) {
+      const int Rc = (int)std::min<size_t>(chunk, qs.size() - r0);
+      rw1.reserve(sizeof(double) * (size_t)Rc * V);
+      rw2.reserve(sizeof(double) * (size_t)Rc * V);
+      double* W[2] = {rw1.as<double>(), rw2.as<double>()};
+      const double* cur = tensor(c0);
+      long cur_stride = 0;
+      int wi = 0;
+      for (int s = 2; s >= 0; --s) {
+        if (!(mask & (1 << s))) continue;
+        const PL& Ps = pl[3 * c0 + s];
+        std::vector<int> ix(Rc);
+        for (int r = 0; r < Rc; ++r) ix[r] = Ps.idx.at(pk[qs[r0 + r]][s]);
+        upload(ctx, idxbuf, ix.data(), sizeof(int) * ix.size());
+        opsA.reserve(sizeof(double) * (size_t)Rc * d[s] * d[s]);
+        gather_rows_f64(ctx, opsA.as<double>(), Ps.ops.as<double>(), idxbuf.as<int>(), Rc, (long)d[s] * d[s]);
+        mode_product_f64(ctx, d, s, opsA.as<double>(), Rc, cur, cur_stride, W[wi], 0.0);
+        cur = W[wi];
+        cur_stride = V;
+        wi ^= 1;
+      }
+      multi_dot(ctx, cur, Rc, V, tensor(c0), dv + filled, nullptr);
+      for (int r = 0; r < Rc; ++r) pos[qs[r0 + r]] = filled + r;
+      filled += Rc;
+    }
+  }
+  // normalise by <T|T> and put the values in probe order
+  ctx->scal.reserve(sizeof(double) * 64);
+  multi_dot(ctx, tensor(c0), 1, V, tensor(c0), ctx->scal.as<double>(), nullptr);
+  scale_vals<<<std::max(1, std::min(1024, (NP + 255) / 256)), 256, 0, ctx->stream>>>(dv, NP, ctx->scal.as<double>());
+  ctx->launches++;
+  idxbuf.reserve(sizeof(int) * std::max(NP, 1));
+  upload(ctx, idxbuf, pos.data(), sizeof(int) * pos.size());
+  rw2.reserve(sizeof(double) * std::max(NP, 1));
+  gather_rows_f64(ctx, rw2.as<double>(), dv, idxbuf.as<int>(), NP, 1);
+  copy_f64(ctx, dv, rw2.as<double>(), NP);
+  ATTN_CHECK_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------ disentangler update
+double attn_state::de_update(const std::vector<std::vector<double>>* u_start, std::vector<double>* rho_out) {
+  const int nDE = (int)des.size();
+  if (!nDE) return 0.0;
+  std::vector<int> owner(model.n_sites, -1);
+  for (int k = 0; k < nDE; ++k) owner[des[k].first] = owner[des[k].second] = k;
+  std::vector<ProbeFactor> F;
+  std::vector<Probe> P;
+  // matrix units on every disentangler site: fid[k][side][x], x = a*2+b for |a><b|
+  std::vector<std::array<std::array<int, 4>, 2>> fid(nDE);
+  for (int k = 0; k < nDE; ++k)
+    for (int side = 0; side < 2; ++side)
+      for (int x = 0; x < 4; ++x) {
+        ProbeFactor f;
+        f.site = side ? des[k].second : des[k].first;
+        for (int i = 0; i < 4; ++i) f.op[i] = (i == x) ? 1.0 : 0.0;
+        fid[k][side][x] = (int)F.size();
+        F.push_back(f);
+      }
+  // M[alpha][beta] = < |beta><alpha| (x) extra >: the probe for (alpha, beta) has
+  // |b_i><a_i| on i and |b_j><a_j| on j (x = b*2 + a), and `extra` (factor id or -1).
+  auto add_block = [&](int k, int extra, std::vector<int>& midx) {
+    midx.resize(16);
+    for (int al = 0; al < 4; ++al)
+      for (int be = 0; be < 4; ++be) {
+        const int ai = al >> 1, aj = al & 1, bi = be >> 1, bj = be & 1;
+        Probe p;
+        p.n = extra >= 0 ? 3 : 2;
+        p.f[0] = fid[k][0][bi * 2 + ai];
+        p.f[1] = fid[k][1][bj * 2 + aj];
+        p.f[2] = extra;
+        midx[al * 4 + be] = (int)P.size();
+        P.push_back(p);
+      }
+  };
+  std::vector<int> rho_idx(16L * nDE), ent_begin(nDE + 1, 0), ent_midx;
+  std::vector<double> ent_C, lambda(nDE, 0.0);
+  std::vector<std::vector<std::pair<std::vector<int>, std::vector<double>>>> ents(nDE);
+  for (int k = 0; k < nDE; ++k) {
+    std::vector<int> m;
+    add_block(k, -1, m);
+    std::copy(m.begin(), m.end(), rho_idx.begin() + 16L * k);
+  }
+  for (const Term& tm : model.terms) {
+    int k = -1;
+    for (int a = 0; a < tm.n; ++a)
+      if (owner[tm.site[a]] >= 0) k = owner[tm.site[a]];
+    if (k < 0) continue;
+    const int i = des[k].first, j = des[k].second;
+    std::vector<int> sites(tm.site, tm.site + tm.n), extra;
+    for (int s : sites)
+      if (s != i && s != j) extra.push_back(s);
+    ATTN_REQUIRE(extra.size() <= 1, ATTN_EUNSUPPORTED, "disentangler update supports terms with <= 1 extra site");
+    {  // spectral norm of the term
+      std::vector<double> U, s, V;
+      const int D = 1 << tm.n;
+      small_svd(tm.op, D, D, U, s, V);
+      lambda[k] += *std::max_element(s.begin(), s.end());
+    }
+    if (extra.empty()) {
+      ents[k].push_back({std::vector<int>(rho_idx.begin() + 16L * k, rho_idx.begin() + 16L * k + 16),
+                         embed_any(tm.op, sites, {i, j})});
+      continue;
+    }
+    const int e = extra[0];
+    std::vector<double> h3 = embed_any(tm.op, sites, {i, j, e});  // order (i, j, e)
+    // R[(al,be)][(ep,ep')] = h3[(al ep)][(be ep')]
+    std::vector<double> R(16 * 4);
+    for (int al = 0; al < 4; ++al)
+      for (int be = 0; be < 4; ++be)
+        for (int ep = 0; ep < 2; ++ep)
+          for (int eq = 0; eq < 2; ++eq) R[(al * 4 + be) * 4 + ep * 2 + eq] = h3[(al * 2 + ep) * 8 + be * 2 + eq];
+    std::vector<double> U, s, Vv;
+    small_svd(R, 16, 4, U, s, Vv);
+    const double smax = *std::max_element(s.begin(), s.end());
+    for (int r = 0; r < 4; ++r) {
+      if (!(s[r] > 1e-14 * smax)) continue;
+      ProbeFactor f;
+      f.site = e;
+      for (int q = 0; q < 4; ++q) f.op[q] = Vv[q * 4 + r];
+      const int fidx = (int)F.size();
+      F.push_back(f);
+      std::vector<int> m;
+      add_block(k, fidx, m);
+      std::vector<double> C(16);
+      for (int q = 0; q < 16; ++q) C[q] = U[q * 4 + r] * s[r];
+      ents[k].push_back({m, C});
+    }
+  }
+  for (int k = 0; k < nDE; ++k) {
+    ATTN_REQUIRE((int)ents[k].size() <= kMaxEnt, ATTN_EUNSUPPORTED, "too many terms on one disentangler");
+    ent_begin[k + 1] = ent_begin[k] + (int)ents[k].size();
+    for (auto& pr : ents[k]) {
+      ent_midx.insert(ent_midx.end(), pr.first.begin(), pr.first.end());
+      ent_C.insert(ent_C.end(), pr.second.begin(), pr.second.end());
+    }
+  }
+  DevBuf vals;
+  probe_expectations(F, P, vals);
+  // device inputs
+  DevBuf d_eb, d_em, d_ec, d_lam, d_rho, d_uin, d_uout, d_e;
+  upload(ctx, d_eb, ent_begin.data(), sizeof(int) * ent_begin.size());
+  upload(ctx, d_em, ent_midx.data(), sizeof(int) * ent_midx.size());
+  upload(ctx, d_ec, ent_C.data(), sizeof(double) * ent_C.size());
+  upload(ctx, d_lam, lambda.data(), sizeof(double) * nDE);
+  upload(ctx, d_rho, rho_idx.data(), sizeof(int) * rho_idx.size());
+  std::vector<double> uin(16L * nDE);
+  const auto& u0 = u_start ? *u_start : us;
+  for (int k = 0; k < nDE; ++k) std::copy(u0[k].begin(), u0[k].end(), uin.begin() + 16L * k);
+  upload(ctx, d_uin, uin.data(), sizeof(double) * uin.size());
+  d_uout.reserve(sizeof(double) * uin.size());
+  d_e.reserve(sizeof(double) * 2 * nDE);
+  DEArgs a;
+  a.n_de = nDE;
+  a.ent_begin = d_eb.as<int>();
+  a.ent_midx = d_em.as<int>();
+  a.ent_C = d_ec.as<double>();
+  a.lambda = d_lam.as<double>();
+  a.rho_idx = d_rho.as<int>();
+  a.vals = vals.as<double>();
+  a.u_in = d_uin.as<double>();
+  a.u_out = d_uout.as<double>();
+  a.e_out = d_e.as<double>();
+  a.max_iter = ctx->cfg.de_max_iter;
+  a.rel_dev = ctx->cfg.de_rel_dev;
+  de_mera_kernel<<<(nDE + 63) / 64, 64, 0, ctx->stream>>>(a);
+  ctx->launches++;
+  ATTN_CHECK_CUDA(cudaGetLastError());
+  std::vector<double> uout(uin.size()), eo(2L * nDE);
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(uout.data(), d_uout.p, sizeof(double) * uout.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(eo.data(), d_e.p, sizeof(double) * eo.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  if (rho_out) {
+    std::vector<double> pv(P.size());
+    ATTN_CHECK_CUDA(cudaMemcpyAsync(pv.data(), vals.p, sizeof(double) * pv.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    rho_out->assign(16L * nDE, 0.0);
+    for (long q = 0; q < 16L * nDE; ++q) (*rho_out)[q] = pv[rho_idx[q]];
+  }
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  double dE = 0.0;
+  for (int k = 0; k < nDE; ++k) {
+    ATTN_REQUIRE(std::isfinite(eo[2 * k + 1]), ATTN_ENONFINITE, "non-finite disentangler energy");
+    us[k].assign(uout.begin() + 16L * k, uout.begin() + 16L * k + 16);
+    dE += eo[2 * k + 1] - eo[2 * k];
+  }
+  last_de_energy.assign(eo.begin(), eo.end());
+  mapped_ready = false;
+  return dE;
+}

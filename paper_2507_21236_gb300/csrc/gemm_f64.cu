@@ -161,7 +161,9 @@ void gemm_f64(attn_ctx* ctx, const GemmF64& g) {
   if (g.M <= 0 || g.N <= 0 || g.Bhi <= 0 || g.Blo <= 0) return;
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, (unsigned)std::min<long>((long)g.Bhi * g.Blo, 65535));
   ATTN_REQUIRE(grid.y <= 65535, ATTN_EUNSUPPORTED, "GEMM M too large");
+  ctx->prof_begin(1);
   gemm_f64_kernel<<<grid, NT, 0, ctx->stream>>>(g);
+  ctx->prof_end(1, 2.0 * g.M * g.N * (double)g.K * g.G * g.Bhi * g.Blo);
   ctx->launches++;
   ATTN_CHECK_CUDA(cudaGetLastError());
 }

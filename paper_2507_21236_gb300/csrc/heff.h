@@ -2,6 +2,29 @@
 #pragma once
 
 #include "attn_internal.h"
+#include "lanczos.h"
+
+// A captured CUDA graph of one eigensolve (Lanczos + optional FP64 refinement)
+// on a fixed start-vector buffer; the buffers it uses are owned here.
+struct EigGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const double* x = nullptr;
+  int depth = 0, dtype = 0, refine = 0;
+  double tol = 0.0, rtol = 0.0;
+  bool prof = false;
+  uint64_t launches = 0;
+  attn::LanczosWork w;
+  std::vector<attn_ctx::GraphEv> evs;
+  ~EigGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto& e : evs) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+  }
+};
 
 // Pair kinds: 0 = slots (0,1) with slice slot 2; 1 = (0,2) slice 1; 2 = (1,2) slice 0.
 static const int kPairP[3] = {0, 0, 1};
@@ -21,6 +44,7 @@ struct attn_heff {
   // Low-precision tensor-core copies (built on first BF16 apply).
   bool tc_ready = false;
   void* tc = nullptr;     // opaque, owned by heff_tc.cu
+  EigGraph* eg = nullptr; // cached eigensolve graph (use_graphs)
   double flops() const;
   void apply_f64(const double* x, double* y);
   void apply_bf16(const double* x, double* y);

@@ -21,7 +21,10 @@ double attn_heff::flops() const {
   return f;
 }
 
-attn_heff::~attn_heff() { attn::tc_release(this); }
+attn_heff::~attn_heff() {
+  delete eg;
+  attn::tc_release(this);
+}
 
 namespace attn {
 

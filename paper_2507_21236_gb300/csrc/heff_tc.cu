@@ -22,6 +22,7 @@
 // clock); on timeout the kernel records an error code, stops issuing work,
 // waits (bounded) for its in-flight copies, frees TMEM and returns.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -396,13 +397,32 @@ __global__ void identity_bf16_kernel(__nv_bfloat16* dst, int m) {
 
 int vgrid(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) / 256, 4096)); }
 
+}  // namespace
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point, so that the
+// library does not link libcuda directly (it loads on machines without a driver).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    ATTN_REQUIRE(e == cudaSuccess && q == cudaDriverEntryPointSuccess && p, ATTN_ECUDA,
+                 "cuTensorMapEncodeTiled is not available from the driver");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+namespace {
+
 // Host: 3-D tiled tensor map over a [D2][D1][D0] bf16 array with a {64, rows, 1} box, 128B swizzle.
 void encode_map(CUtensorMap* map, const void* ptr, int d0, int d1, int d2, int box_rows) {
   cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
   cuuint64_t strides[2] = {(cuuint64_t)d0 * 2, (cuuint64_t)d0 * d1 * 2};
   cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult res = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims,
+  CUresult res = tensor_map_encoder()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims,
                                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -522,7 +542,14 @@ void attn_heff::apply_bf16(const double* x, double* y) {
                                           t->R[2] ? t->x[2].as<__nv_bfloat16>() : nullptr);
   ctx->launches++;
   if (t->grid > 0) {
+    // algorithmic FLOPs of this launch: the pair products and the internal operators
+    double fl = 0.0;
+    for (int k = 0; k < 3; ++k) fl += (double)npair[k] * 2.0 * (m[kPairP[k]] + m[kPairQ[k]]) * V;
+    for (int s = 0; s < 3; ++s)
+      if (has_hint[s]) fl += 2.0 * m[s] * V;
+    ctx->prof_begin(0);
     sandwich_tc_kernel<<<t->grid, kThreads, t->smem, st>>>(t->maps, t->prm);
+    ctx->prof_end(0, fl);
     ctx->launches++;
   }
   combine_kernel<<<vgrid(V), 256, 0, st>>>(y, m[0], m[1], m[2], t->R[0] ? t->y[0].as<float>() : nullptr,

@@ -7,6 +7,13 @@
 // with Sturm counts for the eigenvalue, inverse iteration (tridiagonal
 // Gaussian elimination with partial pivoting) for the eigenvector. Stops when
 // the Ritz residual beta_k |y_k| < tol |theta|, on breakdown, or at `depth`.
+//
+// The whole recurrence is device-resident: beta_k, the Ritz solve and the
+// stop decision are taken by a one-thread kernel after every step and kept in
+// device memory; kernels after the stop see the flag and return, and the
+// final Ritz vector is assembled with the device-side basis size. The host
+// enqueues a fixed sequence of launches (capturable in a CUDA graph) and reads
+// the result once.
 #include <algorithm>
 #include <cmath>
 
@@ -20,13 +27,19 @@ namespace {
 constexpr int LT = 256;
 constexpr int LB = 512;  // blocks for the vector reductions
 
+// scalar slots in the work buffer (doubles)
+constexpr int S_ALPHA = 0, S_BETA = 64, S_TMP = 128, S_DONE = 129, S_NK = 130, S_THETA = 131, S_RESID = 132,
+              S_Y = 192, S_H = 320, S_SIZE = 512;
+
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
 // part[b][i] = partial of <basis_i, w> over block b's grid-stride elements.
-__global__ void multi_dot_partial(const double* basis, int nvec, long V, const double* w, double* part) {
+__global__ void multi_dot_partial(const double* basis, int nvec, long V, const double* w, double* part,
+                                  const double* done) {
+  if (done && *done != 0.0) return;
   __shared__ double sh[LT / 32];
   for (int i = 0; i < nvec; ++i) {
     const double* v = basis + (long)i * V;
@@ -44,8 +57,9 @@ __global__ void multi_dot_partial(const double* basis, int nvec, long V, const d
   }
 }
 
-// out[i] = sum_b part[b][i] (fixed order); optionally out2[i] += out[i].
-__global__ void multi_dot_reduce(const double* part, int nb, int nvec, double* out, double* accum) {
+// out[i] = sum_b part[b][i] (fixed order); optionally accum[i] += out[i].
+__global__ void multi_dot_reduce(const double* part, int nb, int nvec, double* out, double* accum, const double* done) {
+  if (done && *done != 0.0) return;
   int i = blockIdx.x;
   __shared__ double sh[LT / 32];
   double s = 0.0;
@@ -62,7 +76,9 @@ __global__ void multi_dot_reduce(const double* part, int nb, int nvec, double* o
 }
 
 // w -= sum_i coef[i] * basis_i
-__global__ void multi_axpy(double* w, const double* basis, const double* coef, int nvec, long V, double sign) {
+__global__ void multi_axpy(double* w, const double* basis, const double* coef, int nvec, long V, double sign,
+                           const double* done) {
+  if (done && *done != 0.0) return;
   for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) {
     double v = w[e];
     for (int i = 0; i < nvec; ++i) v = fma(-sign * coef[i], basis[(long)i * V + e], v);
@@ -70,17 +86,20 @@ __global__ void multi_axpy(double* w, const double* basis, const double* coef, i
   }
 }
 
-// out = sum_i coef[i] * basis_i
-__global__ void combine(double* out, const double* basis, const double* coef, int nvec, long V) {
+// out = sum_{i < n} coef[i] * basis_i with n = nvec, or (int)*nvec_dev if given
+__global__ void combine(double* out, const double* basis, const double* coef, int nvec, const double* nvec_dev,
+                        long V) {
+  const int n = nvec_dev ? (int)(*nvec_dev) : nvec;
   for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) {
     double v = 0.0;
-    for (int i = 0; i < nvec; ++i) v = fma(coef[i], basis[(long)i * V + e], v);
+    for (int i = 0; i < n; ++i) v = fma(coef[i], basis[(long)i * V + e], v);
     out[e] = v;
   }
 }
 
-// dst = src * (1 / *nrm) where *nrm is a device norm (sqrt applied here if squared)
-__global__ void scale_by_norm(double* dst, const double* src, const double* nrm_sq, long V) {
+// dst = src / sqrt(*nrm_sq) (skipped when *done != 0)
+__global__ void scale_by_norm(double* dst, const double* src, const double* nrm_sq, long V, const double* done) {
+  if (done && *done != 0.0) return;
   double n = sqrt(*nrm_sq);
   double inv = n > 0.0 ? 1.0 / n : 0.0;
   for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) dst[e] = src[e] * inv;
@@ -99,10 +118,8 @@ __device__ int sturm_count(const double* a, const double* b, int n, double x) {
   return c;
 }
 
-// Lowest eigenpair of the n x n symmetric tridiagonal (alpha, beta) -> theta, y, resid = beta_n |y_{n-1}|.
-__global__ void tridiag_lowest(const double* alpha, const double* beta, int n, double beta_next, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  // out layout: [0] theta, [1] resid, [2 .. 2+n) y
+// Lowest eigenpair of the n x n symmetric tridiagonal (alpha, beta): theta and unit y.
+__device__ void tridiag_lowest(const double* alpha, const double* beta, int n, double* theta_out, double* yout) {
   double lo = 1e300, hi = -1e300;
   for (int i = 0; i < n; ++i) {
     double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i < n - 1 ? fabs(beta[i]) : 0.0);
@@ -115,7 +132,7 @@ __global__ void tridiag_lowest(const double* alpha, const double* beta, int n, d
     if (sturm_count(alpha, beta, n, mid) >= 1) hi = mid; else lo = mid;
   }
   const double theta = 0.5 * (lo + hi);
-  // inverse iteration with partial pivoting (up to n = 64)
+  // inverse iteration with partial pivoting (n <= 64)
   double y[64], z[64];
   double dl[64], dd[64], du[64], du2[64];
   int piv[64];
@@ -129,7 +146,6 @@ __global__ void tridiag_lowest(const double* alpha, const double* beta, int n, d
       du2[i] = 0.0;
       z[i] = y[i];
     }
-    // factor (LAPACK-style gttrf without the library): rows i and i+1
     for (int i = 0; i < n - 1; ++i) {
       if (fabs(dd[i]) >= fabs(dl[i])) {
         piv[i] = 0;
@@ -154,7 +170,6 @@ __global__ void tridiag_lowest(const double* alpha, const double* beta, int n, d
     }
     if (dd[n - 1] == 0.0) dd[n - 1] = 1e-300 * scale;
     if (fabs(dd[n - 1]) < 1e-18 * scale) dd[n - 1] = (dd[n - 1] < 0 ? -1.0 : 1.0) * 1e-18 * scale;
-    // solve L U z = y (apply row swaps while eliminating)
     for (int i = 0; i < n - 1; ++i) {
       if (piv[i] == 0) {
         z[i + 1] -= dl[i] * z[i];
@@ -173,110 +188,146 @@ __global__ void tridiag_lowest(const double* alpha, const double* beta, int n, d
     if (!(nrm > 0.0) || !isfinite(nrm)) break;
     for (int i = 0; i < n; ++i) y[i] = z[i] / nrm;
   }
-  // fix the sign: largest-magnitude component positive
   int imax = 0;
   for (int i = 1; i < n; ++i)
     if (fabs(y[i]) > fabs(y[imax])) imax = i;
   double sg = y[imax] < 0 ? -1.0 : 1.0;
-  out[0] = theta;
-  out[1] = fabs(beta_next * y[n - 1]);
-  for (int i = 0; i < n; ++i) out[2 + i] = sg * y[i];
+  *theta_out = theta;
+  for (int i = 0; i < n; ++i) yout[i] = sg * y[i];
+}
+
+// After step k: beta_k = ||w||, Ritz pair of T_{k+1}, stop decision (all on device).
+__global__ void lz_step(double* S, int k, int depth, double tol) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (S[S_DONE] != 0.0) return;
+  const double b = sqrt(fmax(S[S_TMP], 0.0));
+  S[S_BETA + k] = b;
+  const int n = k + 1;
+  double theta, y[64];
+  tridiag_lowest(S + S_ALPHA, S + S_BETA, n, &theta, y);
+  const double resid = fabs(b * y[n - 1]);
+  const double sc = fmax(fabs(theta), 1e-300);
+  const bool stop = resid < tol * sc || b < 1e-14 * sc || k == depth - 1 || !isfinite(theta) || !isfinite(b);
+  S[S_THETA] = theta;
+  S[S_RESID] = resid;
+  S[S_NK] = (double)n;
+  for (int i = 0; i < n; ++i) S[S_Y + i] = y[i];
+  if (stop) S[S_DONE] = 1.0;
+}
+
+__global__ void lz_init(double* S) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    S[S_DONE] = 0.0;
+    S[S_NK] = 1.0;
+    S[S_Y] = 1.0;
+    S[S_THETA] = 0.0;
+    S[S_RESID] = 0.0;
+  }
 }
 
 inline int vgrid(long V) { return (int)std::max<long>(1, std::min<long>((V + LT - 1) / LT, LB)); }
 
-}  // namespace
-
-void multi_dot(attn_ctx* ctx, const double* basis, int nvec, long V, const double* w, double* out, double* accum) {
+void multi_dot_g(attn_ctx* ctx, const double* basis, int nvec, long V, const double* w, double* out, double* accum,
+                 const double* done) {
   const int nb = vgrid(V);
   ctx->partials.reserve(sizeof(double) * (size_t)nb * std::max(nvec, 1));
-  multi_dot_partial<<<nb, LT, 0, ctx->stream>>>(basis, nvec, V, w, ctx->partials.as<double>());
-  multi_dot_reduce<<<nvec, LT, 0, ctx->stream>>>(ctx->partials.as<double>(), nb, nvec, out, accum);
+  multi_dot_partial<<<nb, LT, 0, ctx->stream>>>(basis, nvec, V, w, ctx->partials.as<double>(), done);
+  multi_dot_reduce<<<nvec, LT, 0, ctx->stream>>>(ctx->partials.as<double>(), nb, nvec, out, accum, done);
   ctx->launches += 2;
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
 
+}  // namespace
+
+void multi_dot(attn_ctx* ctx, const double* basis, int nvec, long V, const double* w, double* out, double* accum) {
+  multi_dot_g(ctx, basis, nvec, V, w, out, accum, nullptr);
+}
+
 void multi_axpy_dev(attn_ctx* ctx, double* w, const double* basis, const double* coef, int nvec, long V,
                     double sign) {
-  multi_axpy<<<vgrid(V), LT, 0, ctx->stream>>>(w, basis, coef, nvec, V, sign);
+  multi_axpy<<<vgrid(V), LT, 0, ctx->stream>>>(w, basis, coef, nvec, V, sign, nullptr);
   ctx->launches++;
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
 
 void combine_dev(attn_ctx* ctx, double* out, const double* basis, const double* coef, int nvec, long V) {
-  combine<<<vgrid(V), LT, 0, ctx->stream>>>(out, basis, coef, nvec, V);
+  combine<<<vgrid(V), LT, 0, ctx->stream>>>(out, basis, coef, nvec, nullptr, V);
   ctx->launches++;
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
 
 void normalise_dev(attn_ctx* ctx, double* dst, const double* src, long V, double* nrm_sq_dev) {
   multi_dot(ctx, src, 1, V, src, nrm_sq_dev, nullptr);
-  scale_by_norm<<<vgrid(V), LT, 0, ctx->stream>>>(dst, src, nrm_sq_dev, V);
+  scale_by_norm<<<vgrid(V), LT, 0, ctx->stream>>>(dst, src, nrm_sq_dev, V, nullptr);
   ctx->launches++;
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
 
-LanczosResult lanczos_lowest(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol,
-                             LanczosWork& w) {
+void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol, LanczosWork& w,
+                     int host_check_every) {
   ATTN_REQUIRE(depth >= 1 && depth <= 60, ATTN_EINVAL, "Lanczos depth must be in 1..60");
   w.basis.reserve(sizeof(double) * (size_t)(depth + 1) * V);
   w.wvec.reserve(sizeof(double) * (size_t)V);
-  w.scal.reserve(sizeof(double) * 512);
+  w.scal.reserve(sizeof(double) * S_SIZE);
   double* B = w.basis.as<double>();
   double* W = w.wvec.as<double>();
   double* S = w.scal.as<double>();
-  // S layout: [0..64) alpha, [64..128) beta, [128] tmp, [192..) tridiag out, [320..) h
-  double* alpha = S;
-  double* beta = S + 64;
-  double* tmp = S + 128;
-  double* tri = S + 192;
-  double* h = S + 320;
+  double* done = S + S_DONE;
   cudaStream_t s = ctx->stream;
-  normalise_dev(ctx, B, x, V, tmp);
-  std::vector<double> ha(depth), hb(depth);
-  double host_tri[2 + 64];
-  LanczosResult res{0.0, 0, 0.0, false};
-  int nk = 0;
+  lz_init<<<1, 1, 0, s>>>(S);
+  ctx->launches++;
+  normalise_dev(ctx, B, x, V, S + S_TMP);
   for (int k = 0; k < depth; ++k) {
     double* vk = B + (long)k * V;
     apply(vk, W);
-    multi_dot(ctx, vk, 1, V, W, alpha + k, nullptr);
-    // W -= alpha_k v_k + beta_{k-1} v_{k-1}  (coefficients from device)
-    multi_axpy_dev(ctx, W, vk, alpha + k, 1, V, 1.0);
-    if (k > 0) multi_axpy_dev(ctx, W, B + (long)(k - 1) * V, beta + (k - 1), 1, V, 1.0);
+    multi_dot_g(ctx, vk, 1, V, W, S + S_ALPHA + k, nullptr, done);
+    multi_axpy<<<vgrid(V), LT, 0, s>>>(W, vk, S + S_ALPHA + k, 1, V, 1.0, done);
+    ctx->launches++;
+    if (k > 0) {
+      multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B + (long)(k - 1) * V, S + S_BETA + (k - 1), 1, V, 1.0, done);
+      ctx->launches++;
+    }
     for (int pass = 0; pass < 2; ++pass) {
-      multi_dot(ctx, B, k + 1, V, W, h, nullptr);
-      multi_axpy_dev(ctx, W, B, h, k + 1, V, 1.0);
+      multi_dot_g(ctx, B, k + 1, V, W, S + S_H, nullptr, done);
+      multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H, k + 1, V, 1.0, done);
+      ctx->launches++;
     }
-    multi_dot(ctx, W, 1, V, W, tmp, nullptr);
-    ATTN_CHECK_CUDA(cudaMemcpyAsync(&hb[k], tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
-    ATTN_CHECK_CUDA(cudaStreamSynchronize(s));
-    const double b = std::sqrt(std::max(hb[k], 0.0));
-    nk = k + 1;
-    tridiag_lowest<<<1, 1, 0, s>>>(alpha, beta, nk, b, tri);
+    multi_dot_g(ctx, W, 1, V, W, S + S_TMP, nullptr, done);
+    lz_step<<<1, 1, 0, s>>>(S, k, depth, tol);
     ctx->launches++;
-    ATTN_CHECK_CUDA(cudaMemcpyAsync(host_tri, tri, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
-    ATTN_CHECK_CUDA(cudaStreamSynchronize(s));
-    res.theta = host_tri[0];
-    res.resid = host_tri[1];
-    res.iters = nk;
-    const double sc = std::max(std::fabs(res.theta), 1e-300);
-    ATTN_REQUIRE(std::isfinite(res.theta) && std::isfinite(b), ATTN_ENONFINITE, "non-finite value in Lanczos");
-    if (res.resid < tol * sc || b < 1e-14 * sc) {
-      res.converged = true;
-      break;
+    if (k + 1 < depth) {
+      scale_by_norm<<<vgrid(V), LT, 0, s>>>(B + (long)(k + 1) * V, W, S + S_TMP, V, done);
+      ctx->launches++;
     }
-    if (k == depth - 1) break;
-    // beta_k and v_{k+1} = W / beta_k
-    ATTN_CHECK_CUDA(cudaMemcpyAsync(beta + k, &b, sizeof(double), cudaMemcpyHostToDevice, s));
-    scale_by_norm<<<vgrid(V), LT, 0, s>>>(B + (long)(k + 1) * V, W, tmp, V);
-    ctx->launches++;
+    if (host_check_every > 0 && (k + 1) % host_check_every == 0 && k + 1 < depth) {
+      double hd = 0;
+      ATTN_CHECK_CUDA(cudaMemcpyAsync(&hd, done, sizeof(double), cudaMemcpyDeviceToHost, s));
+      ATTN_CHECK_CUDA(cudaStreamSynchronize(s));
+      if (hd != 0.0) break;
+    }
   }
-  // Ritz vector x = sum_i y_i v_i, normalised
-  combine_dev(ctx, W, B, tri + 2, nk, V);
-  normalise_dev(ctx, x, W, V, tmp);
+  combine<<<vgrid(V), LT, 0, s>>>(W, B, S + S_Y, 0, S + S_NK, V);
+  ctx->launches++;
+  normalise_dev(ctx, x, W, V, S + S_TMP);
   ATTN_CHECK_CUDA(cudaGetLastError());
-  return res;
+}
+
+LanczosResult lanczos_read(attn_ctx* ctx, LanczosWork& w) {
+  double h[8];
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(h, w.scal.as<double>() + S_DONE, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  // h[0] done, h[1] nk, h[2] theta, h[3] resid
+  LanczosResult r{h[2], (int)h[1], h[3], false};
+  ATTN_REQUIRE(std::isfinite(r.theta), ATTN_ENONFINITE, "non-finite value in Lanczos");
+  return r;
+}
+
+LanczosResult lanczos_lowest(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol,
+                             LanczosWork& w) {
+  lanczos_enqueue(ctx, apply, x, V, depth, tol, w, tol > 0.0 ? 5 : 0);
+  LanczosResult r = lanczos_read(ctx, w);
+  r.converged = r.resid < tol * std::max(std::fabs(r.theta), 1e-300);
+  return r;
 }
 
 }  // namespace attn

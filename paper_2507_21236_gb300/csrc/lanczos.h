@@ -24,6 +24,11 @@ struct LanczosResult {
 // length V). On return x holds the unit-norm Ritz vector.
 LanczosResult lanczos_lowest(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol,
                              LanczosWork& w);
+// The same as a fixed launch sequence with no host synchronisation when
+// host_check_every == 0 (capturable); lanczos_read waits and returns the result.
+void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol, LanczosWork& w,
+                     int host_check_every);
+LanczosResult lanczos_read(attn_ctx* ctx, LanczosWork& w);
 
 // out[i] = <basis_i, w> for i < nvec (deterministic two-pass reduction); accum[i] += out[i] if given.
 void multi_dot(attn_ctx* ctx, const double* basis, int nvec, long V, const double* w, double* out, double* accum);

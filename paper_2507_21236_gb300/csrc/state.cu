@@ -273,40 +273,10 @@ void attn_state::renormalise_into(int n, int slot) {
 
   const long budget = 1L << 26;  // doubles per intermediate
   const int chunk = (int)std::max<long>(1, std::min<long>(1024, budget / std::max<long>(V, 1)));
-  auto run_group = [&](const std::vector<int>& ia, const std::vector<int>& ib, long out_off) {
-    const int R = (int)std::max(ia.size(), ib.size());
-    for (int r0 = 0; r0 < R; r0 += chunk) {
-      const int Rc = std::min(chunk, R - r0);
-      rw1.reserve(sizeof(double) * (size_t)Rc * V);
-      rw2.reserve(sizeof(double) * (size_t)Rc * V);
-      double* W1 = rw1.as<double>();
-      double* W2 = rw2.as<double>();
-      const double* cur = Tc;
-      long cur_stride = 0;
-      if (!ib.empty()) {
-        std::vector<int> sub(ib.begin() + r0, ib.begin() + r0 + Rc);
-        upload_idx(ctx, idxbuf, sub);
-        opsB.reserve(sizeof(double) * (size_t)Rc * d[y] * d[y]);
-        gather_rows_f64(ctx, opsB.as<double>(), Ey.ops.as<double>(), idxbuf.as<int>(), Rc, (long)d[y] * d[y]);
-        mode_product_f64(ctx, d, y, opsB.as<double>(), Rc, cur, cur_stride, W1, 0.0);
-        cur = W1;
-        cur_stride = V;
-      }
-      if (!ia.empty()) {
-        std::vector<int> sub(ia.begin() + r0, ia.begin() + r0 + Rc);
-        upload_idx(ctx, idxbuf, sub);
-        opsA.reserve(sizeof(double) * (size_t)Rc * d[x] * d[x]);
-        gather_rows_f64(ctx, opsA.as<double>(), Ex.ops.as<double>(), idxbuf.as<int>(), Rc, (long)d[x] * d[x]);
-        double* dst = (cur == W1) ? W2 : W1;
-        mode_product_f64(ctx, d, x, opsA.as<double>(), Rc, cur, cur_stride, dst, 0.0);
-        cur = dst;
-      }
-      contract_tt(ctx, Tc, d, t, cur, Rc, out.ops.as<double>() + (out_off + r0) * osz);
-    }
-  };
-  run_group(bx, by, 0);
-  run_group(xi, {}, (long)both.size());
-  run_group({}, yi, (long)(both.size() + xonly.size()));
+  renorm_batch(Tc, d, t, x, y, Ex.ops.as<double>(), bx, Ey.ops.as<double>(), by, out.ops.as<double>());
+  renorm_batch(Tc, d, t, x, y, Ex.ops.as<double>(), xi, nullptr, {}, out.ops.as<double>() + (long)both.size() * osz);
+  renorm_batch(Tc, d, t, x, y, nullptr, {}, Ey.ops.as<double>(), yi,
+               out.ops.as<double>() + (long)(both.size() + xonly.size()) * osz);
 
   // internal operator: T^T (H_x (x) 1 + 1 (x) H_y + sum_closed A (x) B) T
   out.has_hint = Ex.has_hint || Ey.has_hint || !closed.empty();
@@ -332,6 +302,46 @@ void attn_state::renormalise_into(int n, int slot) {
     accumulate_slot_f64(ctx, d, x, opsA.as<double>(), Rc, W1, Wsum);
   }
   contract_tt(ctx, Tc, d, t, Wsum, 1, out.hint.as<double>());
+}
+
+// out[r] = T^T (A[ia[r]] on slot x (x) B[ib[r]] on slot y) T over slots x, y
+// (open slot t); an empty index list means the identity on that slot.
+void attn_state::renorm_batch(const double* Tc, const int d[3], int t, int x, int y, const double* Aops,
+                              const std::vector<int>& ia, const double* Bops, const std::vector<int>& ib,
+                              double* out) {
+  const long V = (long)d[0] * d[1] * d[2];
+  const long osz = (long)d[t] * d[t];
+  const long budget = 1L << 26;  // doubles per intermediate
+  const int chunk = (int)std::max<long>(1, std::min<long>(1024, budget / std::max<long>(V, 1)));
+  const int R = (int)std::max(ia.size(), ib.size());
+  for (int r0 = 0; r0 < R; r0 += chunk) {
+    const int Rc = std::min(chunk, R - r0);
+    rw1.reserve(sizeof(double) * (size_t)Rc * V);
+    rw2.reserve(sizeof(double) * (size_t)Rc * V);
+    double* W1 = rw1.as<double>();
+    double* W2 = rw2.as<double>();
+    const double* cur = Tc;
+    long cur_stride = 0;
+    if (!ib.empty()) {
+      std::vector<int> sub(ib.begin() + r0, ib.begin() + r0 + Rc);
+      upload_idx(ctx, idxbuf, sub);
+      opsB.reserve(sizeof(double) * (size_t)Rc * d[y] * d[y]);
+      gather_rows_f64(ctx, opsB.as<double>(), Bops, idxbuf.as<int>(), Rc, (long)d[y] * d[y]);
+      mode_product_f64(ctx, d, y, opsB.as<double>(), Rc, cur, cur_stride, W1, 0.0);
+      cur = W1;
+      cur_stride = V;
+    }
+    if (!ia.empty()) {
+      std::vector<int> sub(ia.begin() + r0, ia.begin() + r0 + Rc);
+      upload_idx(ctx, idxbuf, sub);
+      opsA.reserve(sizeof(double) * (size_t)Rc * d[x] * d[x]);
+      gather_rows_f64(ctx, opsA.as<double>(), Aops, idxbuf.as<int>(), Rc, (long)d[x] * d[x]);
+      double* dst = (cur == W1) ? W2 : W1;
+      mode_product_f64(ctx, d, x, opsA.as<double>(), Rc, cur, cur_stride, dst, 0.0);
+      cur = dst;
+    }
+    contract_tt(ctx, Tc, d, t, cur, Rc, out + (long)r0 * osz);
+  }
 }
 
 // ------------------------------------------------------------------ H_eff

@@ -25,6 +25,16 @@ struct Env {
   int find(int q) const;               // index in ops or -1
 };
 
+// One-site factor of a probe product and a probe (up to three factors on distinct sites).
+struct ProbeFactor {
+  int site;
+  double op[4];
+};
+struct Probe {
+  int n;
+  int f[3];
+};
+
 }  // namespace attn
 
 struct attn_state {
@@ -39,6 +49,8 @@ struct attn_state {
   std::vector<attn::Prod> prods;
   std::vector<attn::Env> env;  // [node*3 + slot]
   bool mapped_ready = false;
+  int sweep_count = 0;
+  std::vector<double> last_de_energy;  // [k][2]: E_k before / after the last update
   attn::QRWork qrw;
   attn::LanczosWork lw, lw2;
   attn::DevBuf colbuf, rbuf, tmpT, idxbuf, opsA, opsB, rw1, rw2;
@@ -54,6 +66,13 @@ struct attn_state {
   attn::Env& get_env(int n, int slot);
   void build_physical_env(int n, int slot);
   void renormalise_into(int n, int slot);
+  void renorm_batch(const double* Tc, const int d[3], int t, int x, int y, const double* Aops,
+                    const std::vector<int>& ia, const double* Bops, const std::vector<int>& ib, double* out);
+  // <psi| prod_s f_s |psi> for rank-1 probes of one-site factors (device results)
+  void probe_expectations(const std::vector<attn::ProbeFactor>& F, const std::vector<attn::Probe>& P,
+                          attn::DevBuf& vals);
+  // MERA-like update of every disentangler (Sec. 4.1.1); returns sum of dE_k
+  double de_update(const std::vector<std::vector<double>>* u_start, std::vector<double>* rho_out);
   attn_heff* build_heff(int n);
   double energy();
   double local_step(int n);
