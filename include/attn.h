@@ -71,6 +71,7 @@ typedef struct attn_ctx attn_ctx;
 typedef struct attn_model attn_model;
 typedef struct attn_state attn_state;
 typedef struct attn_heff attn_heff;
+typedef struct attn_mlp attn_mlp;
 
 /* Run parameters. attn_config_default fills the paper's/our defaults. */
 typedef struct {
@@ -259,6 +260,38 @@ ATTN_API attn_status attn_de_energies(attn_state* st, double* e_out);
  * are placed, update all disentanglers; map H -> H' if needed; then one TTN
  * sweep under H'. *energy receives the last local energy (= E of the state). */
 ATTN_API attn_status attn_sweep(attn_state* st, double* energy);
+
+/* ------------------------------------------------- learned disentangler start
+ * Not in the paper (which starts every disentangler at the identity, Sec. 6):
+ * an FP32 MLP 16 -> 128 -> 128 -> 16 (tanh) maps the two-site reduced density
+ * matrix rho_ij of a disentangler (row-major 4 x 4, first site most
+ * significant) to M; u = expm((M - M^T)/2). Parameters are one FP32 array:
+ * W1[128][16] b1[128] W2[128][128] b2[128] W3[16][128] b3[16]. Training
+ * minimises mean ||u - u_target||_F^2 with Adam; gradients pass through expm
+ * by its Frechet derivative. */
+ATTN_API attn_status attn_mlp_param_count(int* n);
+ATTN_API attn_status attn_mlp_create(attn_ctx* ctx, const float* params_host, attn_mlp** out);
+ATTN_API attn_status attn_mlp_destroy(attn_mlp* m);
+ATTN_API attn_status attn_mlp_get_params(attn_mlp* m, float* params_out);
+/* u_host[n][16] = expm(generator(rho_host[n][16])) */
+ATTN_API attn_status attn_mlp_predict(attn_mlp* m, int n, const double* rho_host, double* u_host);
+/* Loss and its gradient with respect to the parameters (grad_host may be NULL). */
+ATTN_API attn_status attn_mlp_loss_grad(attn_mlp* m, int n, const double* rho_host, const double* u_target_host,
+                                        double* loss, float* grad_host);
+/* `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8) with rate lr. */
+ATTN_API attn_status attn_mlp_train(attn_mlp* m, int n, const double* rho_host, const double* u_target_host,
+                                    int steps, double lr, double* final_loss);
+/* Attach a model (NULL detaches): the first disentangler update of the state
+ * starts each u_k from the prediction, falling back to the plain start when
+ * the prediction is non-finite or raises E_k (the plain method judges it).
+ * The model must outlive its use by the state. */
+ATTN_API attn_status attn_set_learned_init(attn_state* st, attn_mlp* m);
+/* Training pairs of this run: rho_ij recorded at the first disentangler update
+ * (16 doubles per disentangler) and the current u_k, with det(u) = -1 targets
+ * replaced by u diag(1, 1, 1, -1) (unreachable by expm otherwise). */
+ATTN_API attn_status attn_de_training_pairs(attn_state* st, double* rho_out, double* u_out);
+/* How many disentanglers started from the prediction / fell back at the first update. */
+ATTN_API attn_status attn_learned_init_report(attn_state* st, int* used, int* fallback);
 
 #ifdef __cplusplus
 }

@@ -91,6 +91,16 @@ _SIGS = {
     "attn_de_update": [_P, _PD],
     "attn_de_energies": [_P, _PD],
     "attn_sweep": [_P, _PD],
+    "attn_mlp_param_count": [_PI],
+    "attn_mlp_create": [_P, ctypes.POINTER(ctypes.c_float), _PP],
+    "attn_mlp_destroy": [_P],
+    "attn_mlp_get_params": [_P, ctypes.POINTER(ctypes.c_float)],
+    "attn_mlp_predict": [_P, _I, _PD, _PD],
+    "attn_mlp_loss_grad": [_P, _I, _PD, _PD, _PD, ctypes.POINTER(ctypes.c_float)],
+    "attn_mlp_train": [_P, _I, _PD, _PD, _I, _D, _PD],
+    "attn_set_learned_init": [_P, _P],
+    "attn_de_training_pairs": [_P, _PD, _PD],
+    "attn_learned_init_report": [_P, _PI, _PI],
 }
 
 _lib = None
@@ -435,3 +445,71 @@ def attn_sweep(st):
     e = ctypes.c_double()
     _check(load().attn_sweep(st, ctypes.byref(e)))
     return e.value
+
+
+# ------------------------------------------------------- learned initialiser
+_PF = ctypes.POINTER(ctypes.c_float)
+
+
+def attn_mlp_param_count():
+    n = ctypes.c_int()
+    _check(load().attn_mlp_param_count(ctypes.byref(n)))
+    return n.value
+
+
+def attn_mlp_create(ctx, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    m = ctypes.c_void_p()
+    _check(load().attn_mlp_create(ctx, p.ctypes.data_as(_PF), ctypes.byref(m)))
+    return m
+
+
+def attn_mlp_destroy(m):
+    _check(load().attn_mlp_destroy(m))
+
+
+def attn_mlp_get_params(m):
+    out = np.empty(attn_mlp_param_count(), dtype=np.float32)
+    _check(load().attn_mlp_get_params(m, out.ctypes.data_as(_PF)))
+    return out
+
+
+def attn_mlp_predict(m, rho):
+    r, rp = _host_d(np.asarray(rho).reshape(-1, 16))
+    u = np.empty_like(r)
+    _check(load().attn_mlp_predict(m, r.shape[0], rp, u.ctypes.data_as(_PD)))
+    return u.reshape(-1, 4, 4)
+
+
+def attn_mlp_loss_grad(m, rho, ut):
+    r, rp = _host_d(np.asarray(rho).reshape(-1, 16))
+    t, tp = _host_d(np.asarray(ut).reshape(-1, 16))
+    loss = ctypes.c_double()
+    g = np.empty(attn_mlp_param_count(), dtype=np.float32)
+    _check(load().attn_mlp_loss_grad(m, r.shape[0], rp, tp, ctypes.byref(loss), g.ctypes.data_as(_PF)))
+    return loss.value, g
+
+
+def attn_mlp_train(m, rho, ut, steps, lr):
+    r, rp = _host_d(np.asarray(rho).reshape(-1, 16))
+    t, tp = _host_d(np.asarray(ut).reshape(-1, 16))
+    loss = ctypes.c_double()
+    _check(load().attn_mlp_train(m, r.shape[0], rp, tp, steps, lr, ctypes.byref(loss)))
+    return loss.value
+
+
+def attn_set_learned_init(st, m):
+    _check(load().attn_set_learned_init(st, m))
+
+
+def attn_de_training_pairs(st, n_de):
+    rho = np.zeros(16 * max(n_de, 1))
+    u = np.zeros(16 * max(n_de, 1))
+    _check(load().attn_de_training_pairs(st, rho.ctypes.data_as(_PD), u.ctypes.data_as(_PD)))
+    return rho[:16 * n_de].reshape(n_de, 16), u[:16 * n_de].reshape(n_de, 4, 4)
+
+
+def attn_learned_init_report(st):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().attn_learned_init_report(st, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value

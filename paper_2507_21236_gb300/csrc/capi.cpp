@@ -53,7 +53,8 @@ void attn_ctx::prof_begin(int kid) {
     GraphEv g{kid, nullptr, nullptr, 0.0};
     ATTN_CHECK_CUDA(cudaEventCreate(&g.a));
     ATTN_CHECK_CUDA(cudaEventCreate(&g.b));
-    ATTN_CHECK_CUDA(cudaEventRecord(g.a, stream));
+    // an external record becomes an event-record node that fires on every replay
+    ATTN_CHECK_CUDA(cudaEventRecordWithFlags(g.a, stream, cudaEventRecordExternal));
     capture_events->push_back(g);
     return;
   }
@@ -72,7 +73,7 @@ void attn_ctx::prof_end(int kid, double flops) {
   if (!prof_on) return;
   if (capture_events) {
     GraphEv& g = capture_events->back();
-    ATTN_CHECK_CUDA(cudaEventRecord(g.b, stream));
+    ATTN_CHECK_CUDA(cudaEventRecordWithFlags(g.b, stream, cudaEventRecordExternal));
     g.flops = flops;
     return;
   }
@@ -732,6 +733,145 @@ ATTN_API attn_status attn_sweep(attn_state* st, double* energy) {
   ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
   st->sweep_count++;
   if (energy) *energy = e;
+  ATTN_CATCH
+}
+
+// ------------------------------------------------------ learned initialiser
+ATTN_API attn_status attn_mlp_param_count(int* n) {
+  ATTN_TRY
+  NEED(n, "n");
+  *n = (int)mlp_param_count();
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_mlp_create(attn_ctx* ctx, const float* params, attn_mlp** out) {
+  ATTN_TRY
+  NEED(ctx, "ctx");
+  NEED(params, "params_host");
+  NEED(out, "out");
+  for (size_t i = 0; i < mlp_param_count(); ++i)
+    ATTN_REQUIRE(std::isfinite(params[i]), ATTN_ENONFINITE, "non-finite MLP parameter");
+  auto m = std::make_unique<attn_mlp>();
+  m->net.init(ctx, params);
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  *out = m.release();
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_mlp_destroy(attn_mlp* m) {
+  ATTN_TRY
+  if (!m) return ATTN_OK;
+  cudaStreamSynchronize(m->net.ctx->stream);
+  delete m;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_mlp_get_params(attn_mlp* m, float* out) {
+  ATTN_TRY
+  NEED(m, "mlp");
+  NEED(out, "params_out");
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(out, m->net.params.p, sizeof(float) * mlp_param_count(), cudaMemcpyDeviceToHost,
+                                  m->net.ctx->stream));
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(m->net.ctx->stream));
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_mlp_predict(attn_mlp* m, int n, const double* rho, double* u) {
+  ATTN_TRY
+  NEED(m, "mlp");
+  ATTN_REQUIRE(n >= 1, ATTN_EINVAL, "n must be >= 1");
+  NEED(rho, "rho_host");
+  NEED(u, "u_host");
+  m->net.predict(n, rho, u);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_mlp_loss_grad(attn_mlp* m, int n, const double* rho, const double* ut, double* loss,
+                                        float* grad) {
+  ATTN_TRY
+  NEED(m, "mlp");
+  ATTN_REQUIRE(n >= 1, ATTN_EINVAL, "n must be >= 1");
+  NEED(rho, "rho_host");
+  NEED(ut, "u_target_host");
+  m->net.upload_inputs(n, rho, ut);
+  const float l = m->net.loss_grad(n);
+  if (loss) *loss = l;
+  if (grad) {
+    ATTN_CHECK_CUDA(cudaMemcpyAsync(grad, m->net.grad.p, sizeof(float) * mlp_param_count(), cudaMemcpyDeviceToHost,
+                                    m->net.ctx->stream));
+    ATTN_CHECK_CUDA(cudaStreamSynchronize(m->net.ctx->stream));
+  }
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_mlp_train(attn_mlp* m, int n, const double* rho, const double* ut, int steps, double lr,
+                                    double* final_loss) {
+  ATTN_TRY
+  NEED(m, "mlp");
+  ATTN_REQUIRE(n >= 1 && steps >= 0 && lr > 0, ATTN_EINVAL, "need n >= 1, steps >= 0, lr > 0");
+  NEED(rho, "rho_host");
+  NEED(ut, "u_target_host");
+  m->net.upload_inputs(n, rho, ut);
+  float l = 0.f;
+  for (int s = 0; s < steps; ++s) {
+    l = m->net.loss_grad(n);
+    ATTN_REQUIRE(std::isfinite(l), ATTN_ENONFINITE, "non-finite training loss");
+    m->net.adam_step((float)lr);
+  }
+  if (final_loss) *final_loss = steps ? l : m->net.loss_grad(n);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_set_learned_init(attn_state* st, attn_mlp* m) {
+  ATTN_TRY
+  NEED(st, "state");
+  st->learned = m;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_de_training_pairs(attn_state* st, double* rho_out, double* u_out) {
+  ATTN_TRY
+  NEED(st, "state");
+  ATTN_REQUIRE(st->first_de_done, ATTN_EINVAL, "no disentangler update has run on this state");
+  const int n = (int)st->des.size();
+  if (rho_out) std::copy(st->rho_first.begin(), st->rho_first.end(), rho_out);
+  if (u_out) {
+    for (int k = 0; k < n; ++k) {
+      double u[16];
+      std::copy(st->us[k].begin(), st->us[k].end(), u);
+      // det(u) < 0 cannot be reached by expm of an antisymmetric generator:
+      // use u diag(1, 1, 1, -1) as the target (reading)
+      double M[16];
+      std::copy(u, u + 16, M);
+      double det = 1.0;
+      for (int c = 0; c < 4; ++c) {  // Gaussian elimination with partial pivoting
+        int p = c;
+        for (int r = c + 1; r < 4; ++r)
+          if (std::fabs(M[r * 4 + c]) > std::fabs(M[p * 4 + c])) p = r;
+        if (M[p * 4 + c] == 0.0) { det = 0.0; break; }
+        if (p != c) {
+          for (int q = 0; q < 4; ++q) std::swap(M[c * 4 + q], M[p * 4 + q]);
+          det = -det;
+        }
+        det *= M[c * 4 + c];
+        for (int r = c + 1; r < 4; ++r) {
+          const double f = M[r * 4 + c] / M[c * 4 + c];
+          for (int q = c; q < 4; ++q) M[r * 4 + q] -= f * M[c * 4 + q];
+        }
+      }
+      if (det < 0)
+        for (int r = 0; r < 4; ++r) u[r * 4 + 3] = -u[r * 4 + 3];
+      std::copy(u, u + 16, u_out + 16L * k);
+    }
+  }
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_learned_init_report(attn_state* st, int* used, int* fallback) {
+  ATTN_TRY
+  NEED(st, "state");
+  if (used) *used = st->learned_used;
+  if (fallback) *fallback = st->learned_fallback;
   ATTN_CATCH
 }
 

@@ -203,6 +203,13 @@ __global__ void de_mera_kernel(DEArgs a) {
   a.e_out[2 * k + 1] = e;
 }
 
+// E_k of candidate disentanglers (one thread per disentangler)
+__global__ void de_energy_kernel(DEArgs a, const double* u_cand, double* e_out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.n_de) return;
+  e_out[k] = de_energy(a, a.ent_begin[k], a.ent_begin[k + 1], u_cand + 16L * k);
+}
+
 __global__ void scale_vals(double* v, int n, const double* nrm_sq) {
   const double inv = 1.0 / *nrm_sq;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] *= inv;
@@ -577,6 +584,21 @@ double attn_state::de_update(const std::vector<std::vector<double>>* u_start, st
   upload(ctx, d_uin, uin.data(), sizeof(double) * uin.size());
   d_uout.reserve(sizeof(double) * uin.size());
   d_e.reserve(sizeof(double) * 2 * nDE);
+  // reduced density matrices on the disentangler sites (recorded at the first update)
+  std::vector<double> rho_h;
+  if (!first_de_done || rho_out) {
+    std::vector<double> pv(P.size());
+    ATTN_CHECK_CUDA(cudaMemcpyAsync(pv.data(), vals.p, sizeof(double) * pv.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    rho_h.assign(16L * nDE, 0.0);
+    for (long q = 0; q < 16L * nDE; ++q) rho_h[q] = pv[rho_idx[q]];
+    if (rho_out) *rho_out = rho_h;
+  }
+  const bool first = !first_de_done;
+  if (first) {
+    rho_first = rho_h;
+    first_de_done = true;
+  }
   DEArgs a;
   a.n_de = nDE;
   a.ent_begin = d_eb.as<int>();
@@ -590,19 +612,41 @@ double attn_state::de_update(const std::vector<std::vector<double>>* u_start, st
   a.e_out = d_e.as<double>();
   a.max_iter = ctx->cfg.de_max_iter;
   a.rel_dev = ctx->cfg.de_rel_dev;
+  if (first && learned) {
+    // learned start: keep the prediction where it is finite and does not raise E_k
+    std::vector<double> up(16L * nDE);
+    learned->net.predict(nDE, rho_h.data(), up.data());
+    DevBuf d_up, d_ep, d_e0;
+    upload(ctx, d_up, up.data(), sizeof(double) * up.size());
+    d_ep.reserve(sizeof(double) * nDE);
+    d_e0.reserve(sizeof(double) * nDE);
+    de_energy_kernel<<<(nDE + 63) / 64, 64, 0, ctx->stream>>>(a, d_up.as<double>(), d_ep.as<double>());
+    de_energy_kernel<<<(nDE + 63) / 64, 64, 0, ctx->stream>>>(a, d_uin.as<double>(), d_e0.as<double>());
+    ctx->launches += 2;
+    std::vector<double> ep(nDE), e0(nDE);
+    ATTN_CHECK_CUDA(cudaMemcpyAsync(ep.data(), d_ep.p, sizeof(double) * nDE, cudaMemcpyDeviceToHost, ctx->stream));
+    ATTN_CHECK_CUDA(cudaMemcpyAsync(e0.data(), d_e0.p, sizeof(double) * nDE, cudaMemcpyDeviceToHost, ctx->stream));
+    ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    learned_used = learned_fallback = 0;
+    for (int k = 0; k < nDE; ++k) {
+      bool ok = std::isfinite(ep[k]);
+      for (int i = 0; i < 16; ++i) ok = ok && std::isfinite(up[16L * k + i]);
+      if (ok && ep[k] <= e0[k]) {
+        std::copy(up.begin() + 16L * k, up.begin() + 16L * k + 16, uin.begin() + 16L * k);
+        ++learned_used;
+      } else {
+        ++learned_fallback;
+      }
+    }
+    upload(ctx, d_uin, uin.data(), sizeof(double) * uin.size());
+    a.u_in = d_uin.as<double>();
+  }
   de_mera_kernel<<<(nDE + 63) / 64, 64, 0, ctx->stream>>>(a);
   ctx->launches++;
   ATTN_CHECK_CUDA(cudaGetLastError());
   std::vector<double> uout(uin.size()), eo(2L * nDE);
   ATTN_CHECK_CUDA(cudaMemcpyAsync(uout.data(), d_uout.p, sizeof(double) * uout.size(), cudaMemcpyDeviceToHost, ctx->stream));
   ATTN_CHECK_CUDA(cudaMemcpyAsync(eo.data(), d_e.p, sizeof(double) * eo.size(), cudaMemcpyDeviceToHost, ctx->stream));
-  if (rho_out) {
-    std::vector<double> pv(P.size());
-    ATTN_CHECK_CUDA(cudaMemcpyAsync(pv.data(), vals.p, sizeof(double) * pv.size(), cudaMemcpyDeviceToHost, ctx->stream));
-    ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
-    rho_out->assign(16L * nDE, 0.0);
-    for (long q = 0; q < 16L * nDE; ++q) (*rho_out)[q] = pv[rho_idx[q]];
-  }
   ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
   double dE = 0.0;
   for (int k = 0; k < nDE; ++k) {

@@ -7,6 +7,7 @@
 #include "attn_internal.h"
 #include "heff.h"
 #include "lanczos.h"
+#include "mlp.h"
 #include "qr.h"
 
 namespace attn {
@@ -51,6 +52,10 @@ struct attn_state {
   bool mapped_ready = false;
   int sweep_count = 0;
   std::vector<double> last_de_energy;  // [k][2]: E_k before / after the last update
+  bool first_de_done = false;          // the first disentangler update of this state ran
+  std::vector<double> rho_first;       // rho_ij of every disentangler at that first update
+  attn_mlp* learned = nullptr;         // optional learned start for the first update (not owned)
+  int learned_used = 0, learned_fallback = 0;
   attn::QRWork qrw;
   attn::LanczosWork lw, lw2;
   attn::DevBuf colbuf, rbuf, tmpT, idxbuf, opsA, opsB, rw1, rw2;
