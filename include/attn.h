@@ -227,6 +227,26 @@ ATTN_API attn_status attn_heff_apply(attn_heff* h, const double* x_dev, double* 
 /* Same with host buffers: copies x in, applies, copies y out (synchronous). */
 ATTN_API attn_status attn_heff_apply_host(attn_heff* h, const double* x_host, double* y_host, attn_dtype dtype);
 
+/* Allocation-free variant of attn_heff_create + attn_heff_apply(ATTN_F64).
+ * The paper has no counterpart: this is for callers that cannot allocate
+ * device memory -- a host framework may have reserved all free device memory
+ * for its own pool and forbid raw cudaMalloc, or latency-critical code must
+ * not pay the device-wide synchronisation of cudaFree. y_dev = H_eff x_dev
+ * with the operators read in place from the DEVICE arrays of `desc`
+ * (same layout as attn_heff_create), enqueued on cuda_stream (NULL: legacy
+ * default stream). It calls no cudaMalloc or cudaFree; its only scratch is a
+ * file-scope device array of ATTN_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB) that
+ * every GPU loading the library holds until exit. Limits: m0*m1*m2 <=
+ * ATTN_NOALLOC_SCRATCH_DOUBLES, or half of it when n_triple > 0; larger sizes
+ * return ATTN_EINVAL with a message. The first call on each device looks up
+ * the scratch array's device address (with that device current), so make
+ * that first call before any stream capture. Every call shares the one
+ * array: calls whose work overlaps on the GPU (other streams, other threads
+ * on the same device) race and must be serialised by the caller. */
+#define ATTN_NOALLOC_SCRATCH_DOUBLES (1L << 21)
+ATTN_API attn_status attn_heff_apply_f64_static(const attn_heff_desc* desc, const double* x_dev, double* y_dev,
+                                                void* cuda_stream);
+
 /* Lowest eigenpair of H_eff by Lanczos (Sec. 4.4.2) started from T_dev
  * (device [m0][m1][m2]); on return T_dev holds the unit-norm Ritz vector and
  * *theta the Ritz value. Matvecs in the context's matvec_dtype; when that is

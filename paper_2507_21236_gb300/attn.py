@@ -101,6 +101,7 @@ _SIGS = {
     "attn_set_learned_init": [_P, _P],
     "attn_de_training_pairs": [_P, _PD, _PD],
     "attn_learned_init_report": [_P, _PI, _PI],
+    "attn_heff_apply_f64_static": [ctypes.POINTER(attn_heff_desc), _P, _P, _P],
 }
 
 _lib = None
@@ -371,6 +372,28 @@ def attn_heff_create(ctx, m, h_int=(None, None, None), pairs=None, triples=None)
     h = ctypes.c_void_p()
     _check(load().attn_heff_create(ctx, ctypes.byref(d), ctypes.byref(h)))
     return h
+
+
+def _desc(m, h_int=(None, None, None), pairs=None, triples=None):
+    d = attn_heff_desc()
+    for s in range(3):
+        d.m[s] = m[s]
+        d.h_int[s] = _ptr(h_int[s])
+    for k, (a, b) in (pairs or {}).items():
+        d.n_pair[k] = a.shape[0]
+        d.pair_a[k] = _ptr(a)
+        d.pair_b[k] = _ptr(b)
+    if triples is not None:
+        d.n_triple = triples[0].shape[0]
+        for s in range(3):
+            d.triple[s] = _ptr(triples[s])
+    return d
+
+
+def attn_heff_apply_f64_static(m, x_dev, y_dev, h_int=(None, None, None), pairs=None, triples=None, stream=None):
+    """Allocation-free FP64 H_eff apply straight from device operator arrays."""
+    d = _desc(m, h_int, pairs, triples)
+    _check(load().attn_heff_apply_f64_static(ctypes.byref(d), _ptr(x_dev), _ptr(y_dev), stream))
 
 
 def attn_heff_build(st, node):

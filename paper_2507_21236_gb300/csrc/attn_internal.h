@@ -109,6 +109,9 @@ struct GemmF64 {
   double alpha = 1.0, beta = 0.0;
 };
 void gemm_f64(attn_ctx* ctx, const GemmF64& g);
+// The same kernels launched on a bare stream (no context, no allocation).
+cudaError_t gemm_f64_stream(cudaStream_t stream, const GemmF64& g);
+cudaError_t fill_f64_stream(cudaStream_t stream, double* p, size_t n, double v);
 
 // out[r] = mat_r x_slot in[r or shared] for a [m0][m1][m2] tensor; mats is a
 // stack [R][m_s][m_s]; in_stride 0 shares one input, V for per-r inputs.

@@ -168,6 +168,20 @@ void gemm_f64(attn_ctx* ctx, const GemmF64& g) {
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
 
+cudaError_t gemm_f64_stream(cudaStream_t stream, const GemmF64& g) {
+  if (g.M <= 0 || g.N <= 0 || g.Bhi <= 0 || g.Blo <= 0) return cudaSuccess;
+  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, (unsigned)std::min<long>((long)g.Bhi * g.Blo, 65535));
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  gemm_f64_kernel<<<grid, NT, 0, stream>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t fill_f64_stream(cudaStream_t stream, double* p, size_t n, double v) {
+  if (!n) return cudaSuccess;
+  fill_kernel<<<grid_for(n), 256, 0, stream>>>(p, n, v);
+  return cudaGetLastError();
+}
+
 void mode_product_f64(attn_ctx* ctx, const int d[3], int slot, const double* mats, int R, const double* in,
                       long in_stride, double* out, double beta) {
   const long V = (long)d[0] * d[1] * d[2];
