@@ -213,8 +213,68 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweeps(args):
+    """Sweep time to dE/site <= 1e-8: FP64 matvecs vs BF16 matvecs + FP64 refinement,
+    same aTTN schedule (S_TTN = 1) from identical inputs, on one GPU."""
+    import torch
+    from __graft_entry__ import build
+    from inputs import raw_tree_tensors
+    from paper_2507_21236_gb300 import attn
+
+    build()
+    Ls, ms, h = args.sweep_L, args.sweep_m, H_FIELD
+    n = Ls * Ls
+    nL = n.bit_length() - 2
+    cap = lambda e: ms if e >= 5 else min(2 ** (2 ** e), ms)
+    shapes = []
+    for l in range(1, nL + 1):
+        cd = 2 if l == 1 else cap(l - 1)
+        pd = cap(l) if l < nL else cap(nL)
+        shapes += [(cd, cd, pd)] * (n >> l)
+    raw = raw_tree_tensors(shapes, 0)
+    out = {}
+    for mode in ("f64", "mixed"):
+        cfg = attn.attn_config_default()
+        if mode == "mixed":
+            cfg.matvec_dtype = attn.ATTN_BF16
+            cfg.refine_steps = 3
+            cfg.refine_tol = 1e-12
+        ctx = attn.attn_create(cfg, torch.cuda.current_stream().cuda_stream)
+        model = attn.attn_model_tfim(ctx, Ls, h)
+        st = attn.attn_state_create(ctx, model, ms, raw)
+        n_de = attn.attn_de_place(st, n // 4)
+        es, ts = [], []
+        t_conv = None
+        for s in range(args.max_sweeps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            es.append(attn.attn_sweep(st))
+            ts.append(time.perf_counter() - t0)
+            if s >= 2 and abs(es[-1] - es[-2]) / n <= 1e-8 and t_conv is None:
+                t_conv = (s + 1, sum(ts))
+                break
+        out[mode] = {"energies_per_site": [e / n for e in es], "sweep_s": ts,
+                     "sweeps_to_1e-8": t_conv[0] if t_conv else None,
+                     "time_to_1e-8_s": t_conv[1] if t_conv else None, "n_de": n_de}
+        attn.attn_state_destroy(st)
+        attn.attn_model_destroy(model)
+        attn.attn_destroy(ctx)
+    d = abs(out["mixed"]["energies_per_site"][-1] - out["f64"]["energies_per_site"][-1])
+    line = {"metric": "sweep time to dE/site<=1e-8, mixed vs FP64", "unit": "s",
+            "value": out["mixed"]["time_to_1e-8_s"], "higher_is_better": False,
+            "f64_value": out["f64"]["time_to_1e-8_s"], "final_energy_per_site_diff": d,
+            "config": {"workload": f"tfim{Ls}x{Ls}_m{ms}_sweeps", "L": Ls, "m": ms, "h": h,
+                       "s_ttn": 1, "lanczos_depth": 20, "mixed": "bf16 matvecs + 3 FP64 refinement steps"},
+            "runs": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--mode", default="matvec", choices=["matvec", "sweep"])
+    ap.add_argument("--sweep-L", type=int, default=16)
+    ap.add_argument("--sweep-m", type=int, default=32)
+    ap.add_argument("--max-sweeps", type=int, default=30)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
@@ -223,6 +283,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "sweep":
+        return run_sweeps(args)
     args.warmup = max(args.warmup, 3)
 
     import torch

@@ -602,7 +602,8 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
   NEED(theta, "theta");
   attn_ctx* ctx = h->ctx;
   const attn_config& cfg = ctx->cfg;
-  const attn_dtype dt = cfg.matvec_dtype;
+  // shapes the tensor-core tiles cannot take run their matvecs in FP64 (on the GPU)
+  const attn_dtype dt = (cfg.matvec_dtype == ATTN_BF16 && tc_supported(h)) ? ATTN_BF16 : ATTN_F64;
   MatVec lo = [&](const double* a, double* b) {
     if (dt == ATTN_BF16) h->apply_bf16(a, b); else h->apply_f64(a, b);
   };

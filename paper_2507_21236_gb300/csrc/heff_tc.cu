@@ -4,47 +4,71 @@
 // For a pair kind (p, q) with slice slot s, every slice X_s (P x Q, the
 // tensor with slot s fixed) gets
 //     Y_s = sum_r A_r X_s B_r^T      (A_r: P x P on slot p, B_r: Q x Q on slot q)
-// computed per product as two chained MMAs in one CTA:
-//   stage 1:  D1[j][i'] = sum_j' B_r[j][j'] X_s[i'][j']          (M = j, N = i', K = j')
-//   convert:  D1 (FP32, TMEM) -> BF16 Z^T[j][i'] in shared memory (128B swizzle)
-//   stage 2:  D2[i][j] += sum_i' A_r[i][i'] Z^T[j][i']           (M = i, N = j, K = i')
-// D2 = Y_s stays in TMEM across all products of the slice. All operands are
-// K-major with the 128-byte swizzle; TMA brings X_s once and streams A_r, B_r
-// through two-deep rings (separate producer threads for the A and B rings).
-// The stage-1 accumulator is double-buffered in TMEM so that the conversion of
-// product r overlaps stage 1 of product r+1.
+// computed per product as two chained MMAs:
+//   stage 1:  D1[j][i'] = sum_j' B_r[j][j'] X_s[i'][j']     (A = B_r, B = X_s, both in shared memory)
+//   convert:  D1 (FP32) -> BF16 Z^T[j][i'], packed in place in tensor memory
+//   stage 2:  D2[j][i] += sum_i' Z^T[j][i'] A_r[i][i']       (A = Z^T from tensor memory, B = A_r)
+// so D2 = Y_s^T stays in TMEM across all products. Taking the stage-2 A
+// operand from TMEM keeps the stage-1 result out of shared memory, whose
+// bandwidth bounds a 128 x 128 MMA fed from shared memory alone.
 //
-// Warp roles (256 threads): warp 0 = B/X producer, warp 2 = A producer,
-// warp 1 = TMEM allocation + MMA issue, warps 4-7 = conversion and epilogue
-// (warp w reads TMEM lanes 32*(w%4) .. +31). Internal (single-link)
-// operators enter as products with an identity partner; three-link products
-// go through the FP64 path. Every mbarrier wait is bounded (about 2 s of
-// clock); on timeout the kernel records an error code, stops issuing work,
-// waits (bounded) for its in-flight copies, frees TMEM and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-#include <cuda_bf16.h>
-#include <cuda_runtime.h>
-
+// One CTA owns two slices of the same pair kind: every operator tile it loads
+// serves both, which halves the TMA traffic per product. TMEM holds
+// D1 and D2 for each slice (4 x 128 columns). The MMA order is
+//   S1(r, 0), S1(r, 1), S2(r, 0), S2(r, 1), S1(r+1, 0), ...
+// so that converting slice 0 overlaps stage 1 of slice 1 and converting slice 1
+// overlaps stage 2 of slice 0. Operator tiles stream through one ring of 16 KB
+// K-block stages in consumption order (B_r, A_r, B_{r+1}, ...). A slice pair's
+// product list may be split over several CTAs (`rsplit`, chosen by an
+// autotuner at the first application) whose partial Y_s meet by FP32 atomics.
+//
+// Warp roles (640 threads): warp 0 = TMA producer, warp 1 = TMEM allocation
+// and MMA issue, warps 4-19 = conversion and epilogue, eight per slice in two
+// column halves (warp w reads TMEM lanes 32*(w%4) .. +31). Internal
+// (single-link) operators enter as products with an identity partner;
+// three-link products go through the FP64 path. Every mbarrier wait is
+// bounded (about 2 s of clock); on timeout the kernel records an error code,
+// stops issuing work, waits (bounded) for its in-flight copies, frees TMEM and
+// returns.
 #include <algorithm>
 #include <cstring>
 
 #include "heff.h"
+#include "tc_ptx.h"
 
 namespace attn {
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point, so that the
+// library does not link libcuda directly (it loads on machines without a driver).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    ATTN_REQUIRE(e == cudaSuccess && q == cudaDriverEntryPointSuccess && p, ATTN_ECUDA,
+                 "cuTensorMapEncodeTiled is not available from the driver");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kTileBytes = 128 * 128 * 2;  // one 128 x 128 BF16 operand tile (two 64-wide K blocks)
+using namespace tc;
+
+constexpr int kThreads = 640;         // 4 role warps + 16 conversion/epilogue warps
+constexpr int kHalfThreads = 128;     // conversion threads per slice half (Z-full arrivals)
+constexpr int kTileBytes = 128 * 128 * 2;  // one 128 x 128 BF16 tile (two 64-wide K blocks)
 constexpr int kKBlockBytes = 128 * 128;    // 128 rows x 128 bytes
+constexpr int kStages = 10;                // operator ring depth (K blocks)
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct KindParams {
   int P, Q, S, R;     // slice rows/cols, slices, products
+  int rsplit;         // CTAs per slice pair, each owning a contiguous range of products
   int cta_begin;      // first CTA index of this kind
-  float* Y;           // [S][P][Q] fp32 output (written)
+  float* Y;           // [S][P][Q] fp32 output (written, or accumulated when rsplit > 1)
 };
 
 struct TcParams {
@@ -57,101 +81,6 @@ struct TcMaps {
   CUtensorMap x[3], a[3], b[3];
 };
 
-// ------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: returns false (and records `code`) after ~kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, volatile int* abort_flag) {
-  long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
-      atomicCAS(err, 0, code);
-      *abort_flag = 1;
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-          dst),
-      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;                     // descriptor version
-  d |= (uint64_t)2 << 61;                     // 128-byte swizzle
-  return d;
-}
-
-// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major.
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&h);
@@ -160,49 +89,67 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // ------------------------------------------------------------------ kernel
 __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_constant__ TcMaps maps, TcParams prm) {
   extern __shared__ uint8_t smem_raw[];
-  // carve 1024-aligned regions
+  // 1024-aligned regions: X of both slices, operator ring, barriers. X K block kb
+  // holds 256 rows: slice 0 in rows 0..P-1, slice 1 in rows 128..127+P.
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
-  const uint32_t sX = base;                       // 32 KB
-  const uint32_t sB = sX + kTileBytes;            // 2 x 32 KB
-  const uint32_t sA = sB + 2 * kTileBytes;        // 2 x 32 KB
-  const uint32_t sZ = sA + 2 * kTileBytes;        // 32 KB
-  uint8_t* gZ = gbase + (sZ - base);
-  const uint32_t sBar = sZ + kTileBytes;          // barriers
+  const uint32_t sX = base;
+  const uint32_t sRing = base + 2 * kTileBytes;
+  const uint32_t sBar = sRing + kStages * kKBlockBytes;
+  enum {
+    XFULL = 0,
+    FULL = 1,
+    EMPTY = 1 + kStages,
+    D1FULL = 1 + 2 * kStages,  // stage 1 of both slices done
+    ZFULL = 2 + 2 * kStages,   // [slice][half]: that half of Z^T packed in TMEM
+    D2FULL = 6 + 2 * kStages,
+    NBAR = 7 + 2 * kStages
+  };
   uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + (sBar - base));
-  // barrier indices
-  enum { XFULL = 0, BFULL = 1, BEMPTY = 3, AFULL = 5, AEMPTY = 7, D1FULL = 9, ZFULL = 11, ZEMPTY = 12, D2FULL = 13,
-         NBAR = 14 };
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto bar = [&](int i) { return sBar + 8u * (uint32_t)i; };
 
-  // which kind / slice does this CTA own?
+  // which kind / slice pair / product range does this CTA own?
+  // (static indices only: a runtime index into the parameter struct would copy it to local memory)
   int kind = 0;
-  for (int k = 1; k < prm.nkinds; ++k)
-    if ((int)blockIdx.x >= prm.kind[k].cta_begin) kind = k;
-  const KindParams kp = prm.kind[kind];
-  const int s = blockIdx.x - kp.cta_begin;
-  const int P = kp.P, Q = kp.Q, R = kp.R;
+  KindParams kp = prm.kind[0];
+  if (prm.nkinds > 1 && (int)blockIdx.x >= prm.kind[1].cta_begin) { kind = 1; kp = prm.kind[1]; }
+  if (prm.nkinds > 2 && (int)blockIdx.x >= prm.kind[2].cta_begin) { kind = 2; kp = prm.kind[2]; }
+  const int local = blockIdx.x - kp.cta_begin;
+  const int pair = local / kp.rsplit, part = local % kp.rsplit;
+  const int s0 = 2 * pair;
+  const int nsl = (s0 + 1 < kp.S) ? 2 : 1;
+  const int r_begin = (int)((long)kp.R * part / kp.rsplit);
+  const int R = (int)((long)kp.R * (part + 1) / kp.rsplit) - r_begin;
+  const int P = kp.P, Q = kp.Q;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     mbar_init(bar(XFULL), 1);
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(bar(BFULL + i), 1);
-      mbar_init(bar(BEMPTY + i), 1);
-      mbar_init(bar(AFULL + i), 1);
-      mbar_init(bar(AEMPTY + i), 1);
-      mbar_init(bar(D1FULL + i), 1);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(bar(FULL + i), 1);
+      mbar_init(bar(EMPTY + i), 1);
     }
-    mbar_init(bar(ZFULL), 128);
-    mbar_init(bar(ZEMPTY), 1);
+    mbar_init(bar(D1FULL), 1);
+    for (int i = 0; i < 4; ++i) mbar_init(bar(ZFULL + i), kHalfThreads);
     mbar_init(bar(D2FULL), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
+  if (P < 128) {
+    // rows P..127 of each slice's X block are not loaded; zero them so that the
+    // unused stage-1 columns hold finite values
+    const int nkb = (Q + 63) / 64;
+    for (int e = threadIdx.x; e < nkb * 2 * (128 - P) * 8; e += blockDim.x) {
+      const int c16 = e & 7, row = (e >> 3) % (128 - P), rest = (e >> 3) / (128 - P);
+      const int u = rest & 1, kblk = rest >> 1;
+      *reinterpret_cast<uint4*>(gbase + kblk * 2 * kTileBytes / 2 + u * (kTileBytes / 2) + (P + row) * 128 + c16 * 16) =
+          make_uint4(0, 0, 0, 0);
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kTmemCols));
@@ -212,132 +159,136 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tD1[2] = {tmem, tmem + 128};
-  const uint32_t tD2 = tmem + 256;
+  // TMEM: D1 of slice u in columns 128u .. 128u+P-1 (Z^T packed in place), D2 of slice u at 256 + 128u
+  auto tD2 = [&](int u) { return tmem + 256u + 128u * (uint32_t)u; };
   const int nkbQ = (Q + 63) / 64, nkbP = (P + 63) / 64;
   const CUtensorMap* mX = &maps.x[kind];
   const CUtensorMap* mA = &maps.a[kind];
   const CUtensorMap* mB = &maps.b[kind];
 
   if (warp == 0 && lane == 0) {
-    // ---- X and B producer
-    mbar_expect_tx(bar(XFULL), (uint32_t)(nkbQ * P * 128));
-    for (int kb = 0; kb < nkbQ; ++kb) tma_load_3d(sX + kb * (P * 128), mX, 64 * kb, 0, s, bar(XFULL));
-    int issued = 0;
-    for (int r = 0; r < R; ++r) {
-      const int slot = r & 1;
-      if (r >= 2 && !mbar_wait(bar(BEMPTY + slot), ((r >> 1) - 1) & 1, prm.err, 11, abort_flag)) break;
-      mbar_expect_tx(bar(BFULL + slot), (uint32_t)(nkbQ * kKBlockBytes));
+    // ---- producer: X of both slices once, then operator K blocks in consumption order
+    mbar_expect_tx(bar(XFULL), (uint32_t)(nsl * nkbQ * P * 128));
+    for (int u = 0; u < nsl; ++u)
       for (int kb = 0; kb < nkbQ; ++kb)
-        tma_load_3d(sB + slot * kTileBytes + kb * kKBlockBytes, mB, 64 * kb, 0, r, bar(BFULL + slot));
-      issued = r + 1;
+        tma_load_3d(sX + kb * kTileBytes + u * (kTileBytes / 2), mX, 64 * kb, 0, s0 + u, bar(XFULL));
+    int issued = 0;
+    bool ok = true;
+    for (int r = 0; ok && r < R; ++r) {
+      for (int half = 0; ok && half < 2; ++half) {
+        const CUtensorMap* mp = half == 0 ? mB : mA;
+        const int nkb = half == 0 ? nkbQ : nkbP;
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int st = issued % kStages;
+          if (issued >= kStages &&
+              !mbar_wait(bar(EMPTY + st), ((issued / kStages) - 1) & 1, prm.err, 11, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(bar(FULL + st), (uint32_t)kKBlockBytes);
+          tma_load_3d(sRing + st * kKBlockBytes, mp, 64 * kb, 0, r_begin + r, bar(FULL + st));
+          ++issued;
+        }
+      }
     }
     // drain: wait (bounded) until every issued load has landed
-    mbar_wait(bar(XFULL), 0, prm.err, 12, abort_flag);
-    for (int r = (issued >= 2 ? issued - 2 : 0); r < issued; ++r) {
+    {
       long long t0 = clock64();
-      while (!mbar_try_wait(bar(BFULL + (r & 1)), (r >> 1) & 1) && clock64() - t0 < kWaitCycles) {}
+      while (!mbar_try_wait(bar(XFULL), 0) && clock64() - t0 < kWaitCycles) {}
     }
-  } else if (warp == 2 && lane == 0) {
-    // ---- A producer
-    int issued = 0;
-    for (int r = 0; r < R; ++r) {
-      const int slot = r & 1;
-      if (r >= 2 && !mbar_wait(bar(AEMPTY + slot), ((r >> 1) - 1) & 1, prm.err, 21, abort_flag)) break;
-      mbar_expect_tx(bar(AFULL + slot), (uint32_t)(nkbP * kKBlockBytes));
-      for (int kb = 0; kb < nkbP; ++kb)
-        tma_load_3d(sA + slot * kTileBytes + kb * kKBlockBytes, mA, 64 * kb, 0, r, bar(AFULL + slot));
-      issued = r + 1;
-    }
-    for (int r = (issued >= 2 ? issued - 2 : 0); r < issued; ++r) {
+    for (int q = (issued > kStages ? issued - kStages : 0); q < issued; ++q) {
       long long t0 = clock64();
-      while (!mbar_try_wait(bar(AFULL + (r & 1)), (r >> 1) & 1) && clock64() - t0 < kWaitCycles) {}
+      while (!mbar_try_wait(bar(FULL + q % kStages), (q / kStages) & 1) && clock64() - t0 < kWaitCycles) {}
     }
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    const uint32_t id1 = idesc_bf16(128, P);
-    const uint32_t id2 = idesc_bf16(128, Q);
+    // ---- MMA issuer. Stage 1 covers both slices in one N = 128 + P instruction
+    // stream (N = P for a lone slice); stage 2 runs per slice with N = P.
+    const uint32_t id1 = idesc_bf16(128, nsl == 2 ? 128 + P : P);
+    const uint32_t id2 = idesc_bf16(128, P);
     bool ok = mbar_wait(bar(XFULL), 0, prm.err, 31, abort_flag);
-    for (int r = 0; ok && r <= R; ++r) {
-      if (r < R) {
-        const int slot = r & 1;
-        if (!mbar_wait(bar(BFULL + slot), (r >> 1) & 1, prm.err, 32, abort_flag)) break;
+    int pos = 0;
+    for (int r = 0; ok && r < R; ++r) {
+      const int posB = pos, posA = pos + nkbQ;
+      pos += nkbQ + nkbP;
+      // stage 1: D1 = B_r [X_0; X_1]^T. D1 still holds Z of product r-1, but every
+      // stage-2 MMA reading it was issued earlier and MMAs of one thread run in order.
+      for (int kb = 0; kb < nkbQ; ++kb) {
+        const int q = posB + kb, st = q % kStages;
+        if (!mbar_wait(bar(FULL + st), (q / kStages) & 1, prm.err, 32, abort_flag)) { ok = false; break; }
         fence_after();
-        const uint32_t aB = sB + slot * kTileBytes;
-        for (int k = 0; k < Q / 16; ++k) {
-          const uint32_t off = (k >> 2) * kKBlockBytes + (k & 3) * 32;
-          const uint32_t offX = (k >> 2) * (P * 128) + (k & 3) * 32;
-          mma_bf16(tD1[r & 1], sw128_desc(aB + off), sw128_desc(sX + offX), id1, k > 0);
-        }
-        mma_commit(bar(BEMPTY + slot));
-        mma_commit(bar(D1FULL + (r & 1)));
+        const uint32_t aB = sRing + st * kKBlockBytes, aX = sX + kb * kTileBytes;
+        for (int k4 = 0; k4 < 4 && kb * 4 + k4 < Q / 16; ++k4)
+          mma_bf16(tmem, sw128_desc(aB + 32 * k4), sw128_desc(aX + 32 * k4), id1, (kb > 0 || k4 > 0));
+        mma_commit(bar(EMPTY + st));
       }
-      if (r >= 1) {
-        const int rr = r - 1, slot = rr & 1;
-        if (!mbar_wait(bar(AFULL + slot), (rr >> 1) & 1, prm.err, 33, abort_flag)) break;
-        if (!mbar_wait(bar(ZFULL), rr & 1, prm.err, 34, abort_flag)) break;
-        fence_after();
-        const uint32_t aA = sA + slot * kTileBytes;
-        for (int k = 0; k < P / 16; ++k) {
-          const uint32_t off = (k >> 2) * kKBlockBytes + (k & 3) * 32;
-          const uint32_t offZ = (k >> 2) * (Q * 128) + (k & 3) * 32;
-          mma_bf16(tD2, sw128_desc(aA + off), sw128_desc(sZ + offZ), id2, (rr > 0 || k > 0) ? 1u : 0u);
+      if (!ok) break;
+      mma_commit(bar(D1FULL));
+      // stage 2 per slice: D2_u += Z_u^T A_r^T, Z_u read from TMEM half by half
+      for (int u = 0; ok && u < nsl; ++u) {
+        for (int kb = 0; kb < nkbP; ++kb) {
+          const int q = posA + kb, st = q % kStages;
+          if (!mbar_wait(bar(ZFULL + 2 * u + kb), r & 1, prm.err, 34, abort_flag)) { ok = false; break; }
+          if (u == 0 && !mbar_wait(bar(FULL + st), (q / kStages) & 1, prm.err, 33, abort_flag)) { ok = false; break; }
+          fence_after();
+          const uint32_t aA = sRing + st * kKBlockBytes;
+          const uint32_t aZ = tmem + 128u * (uint32_t)u + 64u * (uint32_t)kb;
+          for (int k4 = 0; k4 < 4; ++k4) {
+            const int kk = kb * 4 + k4;  // K step over i' (16 wide, 8 packed TMEM columns)
+            if (kk < P / 16)
+              mma_bf16_ts(tD2(u), aZ + 8 * k4, sw128_desc(aA + 32 * k4), id2, (r > 0 || kk > 0) ? 1u : 0u);
+          }
+          if (u == nsl - 1) mma_commit(bar(EMPTY + st));
         }
-        mma_commit(bar(AEMPTY + slot));
-        mma_commit(bar(ZEMPTY));
       }
     }
     mma_commit(bar(D2FULL));
     // every MMA this thread issued must finish before TMEM can be freed
-    {
-      long long t0 = clock64();
-      while (!mbar_try_wait(bar(D2FULL), 0) && clock64() - t0 < kWaitCycles) {}
-    }
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar(D2FULL), 0) && clock64() - t0 < kWaitCycles) {}
   } else if (warp >= 4) {
-    // ---- conversion D1 -> Z^T (bf16, swizzled) and the epilogue
+    // ---- conversion D1 -> packed BF16 Z^T and the epilogue. Slice u has warps
+    // 4+8u .. 11+8u; warps of half hh own the 64 columns from 64 hh of the slice's
+    // D1 and pack them into the first 32 of those columns (nothing else reads them).
+    const int cw = warp - 4;
+    const int u = cw >> 3, hh = (cw >> 2) & 1;
     const int q4 = warp & 3;
-    const int j = q4 * 32 + lane;  // TMEM lane == row of D1 (j) and of D2 (i)
+    const int j = q4 * 32 + lane;  // TMEM lane == row j of D1 and of D2 = Y^T
     const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
-    bool ok = true;
-    for (int r = 0; r < R && ok; ++r) {
-      if (!mbar_wait(bar(D1FULL + (r & 1)), (r >> 1) & 1, prm.err, 41, abort_flag)) { ok = false; break; }
-      if (r >= 1 && !mbar_wait(bar(ZEMPTY), (r - 1) & 1, prm.err, 42, abort_flag)) { ok = false; break; }
+    const int c0 = 64 * hh;
+    const uint32_t tz = tmem + lane_off + 128u * (uint32_t)u + (uint32_t)c0;
+    bool ok = u < nsl && c0 < P;
+    for (int r = 0; ok && r < R; ++r) {
+      // warp-uniform: the TMEM accesses below are .sync.aligned
+      if (!__all_sync(0xffffffffu, mbar_wait(bar(D1FULL), r & 1, prm.err, 41, abort_flag))) { ok = false; break; }
       fence_after();
-      for (int c0 = 0; c0 < P; c0 += 32) {
+      uint32_t w[32];  // packed BF16 pairs of this thread's 64 columns
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
         float v[32];
-        tmem_ld32(tD1[r & 1] + lane_off + c0, v);
+        tmem_ld32(tz + 32 * t, v);
+#pragma unroll
+        for (int h = 0; h < 16; ++h) w[16 * t + h] = pack_bf16(v[2 * h], v[2 * h + 1]);
+      }
+      tmem_st32(tz, w);
+      fence_before();
+      mbar_arrive(bar(ZFULL + 2 * u + hh));
+    }
+    if (ok && R > 0 && __all_sync(0xffffffffu, mbar_wait(bar(D2FULL), 0, prm.err, 43, abort_flag))) {
+      fence_after();
+      float* yp = kp.Y + ((long)(s0 + u) * P + c0) * Q + j;  // walks down column j of Y_s
+      const bool add = kp.rsplit > 1;  // partial sums of a split product list meet here
+      for (int cc = c0; cc < c0 + 64 && cc < P; cc += 32) {
+        float v[32];
+        tmem_ld32(tD2(u) + lane_off + cc, v);  // v[c] = Y_s[cc + c][j]
         if (j < Q) {
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {  // four 16-byte chunks of 8 elements
-            const int i0 = c0 + 8 * h;   // column index i'
-            const int kb = i0 >> 6, chunk = (i0 & 63) >> 3;
-            uint4 w;
-            w.x = pack_bf16(v[8 * h + 0], v[8 * h + 1]);
-            w.y = pack_bf16(v[8 * h + 2], v[8 * h + 3]);
-            w.z = pack_bf16(v[8 * h + 4], v[8 * h + 5]);
-            w.w = pack_bf16(v[8 * h + 6], v[8 * h + 7]);
-            const uint32_t off = kb * (Q * 128) + (j >> 3) * 1024 + (j & 7) * 128 + ((chunk ^ (j & 7)) << 4);
-            *reinterpret_cast<uint4*>(gZ + off) = w;
+          for (int c = 0; c < 32; ++c) {
+            if (cc + c < P) {
+              if (add) atomicAdd(yp, v[c]);
+              else *yp = v[c];
+            }
+            yp += Q;
           }
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      fence_before();
-      mbar_arrive(bar(ZFULL));
-    }
-    if (ok && mbar_wait(bar(D2FULL), 0, prm.err, 43, abort_flag)) {
-      fence_after();
-      const int i = j;
-      float* yrow = kp.Y + ((long)s * P + i) * Q;
-      for (int c0 = 0; c0 < Q; c0 += 32) {
-        float v[32];
-        tmem_ld32(tD2 + lane_off + c0, v);
-        if (i < P) {
-#pragma unroll
-          for (int h = 0; h < 8; ++h)
-            if (c0 + 4 * h < Q)
-              *reinterpret_cast<float4*>(yrow + c0 + 4 * h) =
-                  make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
         }
       }
     }
@@ -383,8 +334,6 @@ __global__ void combine_kernel(double* y, int m0, int m1, int m2, const float* y
   }
 }
 
-// dst[r] = bf16(src[r]) for r < R (stack of m x m), plus optional extra slices:
-// identity (mode 1) or a given matrix (mode 2) appended.
 __global__ void to_bf16_kernel(__nv_bfloat16* dst, const double* src, long n) {
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
     dst[e] = __double2bfloat16(src[e]);
@@ -397,25 +346,6 @@ __global__ void identity_bf16_kernel(__nv_bfloat16* dst, int m) {
 
 int vgrid(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) / 256, 4096)); }
 
-}  // namespace
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point, so that the
-// library does not link libcuda directly (it loads on machines without a driver).
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
-    ATTN_REQUIRE(e == cudaSuccess && q == cudaDriverEntryPointSuccess && p, ATTN_ECUDA,
-                 "cuTensorMapEncodeTiled is not available from the driver");
-    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-namespace {
-
 // Host: 3-D tiled tensor map over a [D2][D1][D0] bf16 array with a {64, rows, 1} box, 128B swizzle.
 void encode_map(CUtensorMap* map, const void* ptr, int d0, int d1, int d2, int box_rows) {
   cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
@@ -423,9 +353,8 @@ void encode_map(CUtensorMap* map, const void* ptr, int d0, int d1, int d2, int b
   cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult res = tensor_map_encoder()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims,
-                                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   ATTN_REQUIRE(res == CUDA_SUCCESS, ATTN_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)res) + ")");
 }
 
@@ -442,7 +371,26 @@ struct TcState {
   TcParams prm;
   int grid = 0;
   size_t smem = 0;
-  bool fp64_triples = false;
+  int rsplit = 1;        // products of a slice split over this many CTAs (autotuned)
+  bool tuned = false;
+  // Split every kind's product list f ways (at least 8 products per CTA) and lay out
+  // the grid: one CTA per slice pair and product range.
+  void set_split(int f) {
+    int cta = 0;
+    for (int k = 0; k < prm.nkinds; ++k) {
+      KindParams& kp = prm.kind[k];
+      kp.rsplit = std::max(1, std::min(f, kp.R / 8));
+      kp.cta_begin = cta;
+      cta += (kp.S + 1) / 2 * kp.rsplit;
+    }
+    grid = cta;
+    rsplit = f;
+  }
+  bool split_any() const {
+    for (int k = 0; k < prm.nkinds; ++k)
+      if (prm.kind[k].rsplit > 1) return true;
+    return false;
+  }
 };
 
 bool tc_supported(const attn_heff* h) {
@@ -502,17 +450,13 @@ static void tc_build(attn_heff* h) {
     const int S = m[sl];
     t->x[k].reserve(sizeof(__nv_bfloat16) * (size_t)h->V);
     t->y[k].reserve(sizeof(float) * (size_t)h->V);
-    encode_map(&t->maps.x[k], t->x[k].p, Q, P, S, P);
-    encode_map(&t->maps.a[k], t->a[k].p, P, P, R, 128);
-    encode_map(&t->maps.b[k], t->b[k].p, Q, Q, R, 128);
+    encode_map(&t->maps.x[nk], t->x[k].p, Q, P, S, P);
+    encode_map(&t->maps.a[nk], t->a[k].p, P, P, R, 128);
+    encode_map(&t->maps.b[nk], t->b[k].p, Q, Q, R, 128);
     KindParams& kp = t->prm.kind[nk];
     kp.P = P; kp.Q = Q; kp.S = S; kp.R = R; kp.cta_begin = cta; kp.Y = t->y[k].as<float>();
-    if (nk != k) {
-      t->maps.x[nk] = t->maps.x[k];
-      t->maps.a[nk] = t->maps.a[k];
-      t->maps.b[nk] = t->maps.b[k];
-    }
-    cta += S;
+    kp.rsplit = 1;
+    cta += (S + 1) / 2;
     ++nk;
   }
   t->prm.nkinds = nk;
@@ -520,10 +464,21 @@ static void tc_build(attn_heff* h) {
   t->err.reserve(sizeof(int));
   ATTN_CHECK_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), st));
   t->prm.err = t->err.as<int>();
-  t->smem = 1024 + 6 * (size_t)kTileBytes + 256;
+  t->smem = 1024 + 2 * (size_t)kTileBytes + (size_t)kStages * kKBlockBytes + 256;
   ATTN_CHECK_CUDA(cudaFuncSetAttribute(sandwich_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem));
   ATTN_CHECK_CUDA(cudaGetLastError());
   h->tc_ready = true;
+}
+
+// Read and clear the tensor-core error word of an H_eff (0 = ok).
+int tc_error(attn_heff* h) {
+  if (!h->tc_ready) return 0;
+  TcState* t = static_cast<TcState*>(h->tc);
+  int e = 0;
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(&e, t->err.p, sizeof(int), cudaMemcpyDeviceToHost, h->ctx->stream));
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(h->ctx->stream));
+  if (e) ATTN_CHECK_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), h->ctx->stream));
+  return e;
 }
 
 }  // namespace attn
@@ -541,12 +496,50 @@ void attn_heff::apply_bf16(const double* x, double* y) {
                                           t->R[1] ? t->x[1].as<__nv_bfloat16>() : nullptr,
                                           t->R[2] ? t->x[2].as<__nv_bfloat16>() : nullptr);
   ctx->launches++;
+  auto zero_split_outputs = [&]() {
+    for (int k = 0; k < 3; ++k)
+      if (t->R[k]) ATTN_CHECK_CUDA(cudaMemsetAsync(t->y[k].p, 0, sizeof(float) * (size_t)V, st));
+  };
+  if (t->grid > 0 && !t->tuned) {
+    // Autotuner: time the candidate product splits on this H_eff's real input and
+    // keep the fastest (one-off, at the first BF16 application).
+    cudaEvent_t e0, e1;
+    ATTN_CHECK_CUDA(cudaEventCreate(&e0));
+    ATTN_CHECK_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_f = 1;
+    for (int f : {1, 2, 3, 4, 5, 6, 8, 10, 12}) {
+      t->set_split(f);
+      if (f > 1 && !t->split_any()) continue;
+      float tot = 0.f;
+      for (int rep = 0; rep < 3; ++rep) {
+        if (t->split_any()) zero_split_outputs();
+        ATTN_CHECK_CUDA(cudaEventRecord(e0, st));
+        sandwich_tc_kernel<<<t->grid, kThreads, t->smem, st>>>(t->maps, t->prm);
+        ATTN_CHECK_CUDA(cudaEventRecord(e1, st));
+        ATTN_CHECK_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        ATTN_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) tot += ms;
+        ctx->launches++;
+      }
+      if (tot < best) {
+        best = tot;
+        best_f = f;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    t->set_split(best_f);
+    t->tuned = true;
+  }
   if (t->grid > 0) {
     // algorithmic FLOPs of this launch: the pair products and the internal operators
     double fl = 0.0;
     for (int k = 0; k < 3; ++k) fl += (double)npair[k] * 2.0 * (m[kPairP[k]] + m[kPairQ[k]]) * V;
     for (int s = 0; s < 3; ++s)
       if (has_hint[s]) fl += 2.0 * m[s] * V;
+    if (t->split_any()) zero_split_outputs();
     ctx->prof_begin(0);
     sandwich_tc_kernel<<<t->grid, kThreads, t->smem, st>>>(t->maps, t->prm);
     ctx->prof_end(0, fl);
@@ -574,16 +567,3 @@ void attn_heff::apply_bf16(const double* x, double* y) {
     }
   }
 }
-
-namespace attn {
-// Read and clear the tensor-core error word of an H_eff (0 = ok).
-int tc_error(attn_heff* h) {
-  if (!h->tc_ready) return 0;
-  TcState* t = static_cast<TcState*>(h->tc);
-  int e = 0;
-  ATTN_CHECK_CUDA(cudaMemcpyAsync(&e, t->err.p, sizeof(int), cudaMemcpyDeviceToHost, h->ctx->stream));
-  ATTN_CHECK_CUDA(cudaStreamSynchronize(h->ctx->stream));
-  if (e) ATTN_CHECK_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), h->ctx->stream));
-  return e;
-}
-}  // namespace attn

@@ -29,7 +29,7 @@ constexpr int LB = 512;  // blocks for the vector reductions
 
 // scalar slots in the work buffer (doubles)
 constexpr int S_ALPHA = 0, S_BETA = 64, S_TMP = 128, S_DONE = 129, S_NK = 130, S_THETA = 131, S_RESID = 132,
-              S_Y = 192, S_H = 320, S_SIZE = 512;
+              S_Y = 192, S_H = 320, S_H2 = 400, S_SIZE = 512;
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -119,18 +119,30 @@ __device__ int sturm_count(const double* a, const double* b, int n, double x) {
 }
 
 // Lowest eigenpair of the n x n symmetric tridiagonal (alpha, beta): theta and unit y.
+// Called by all 32 lanes of one warp: each bisection round evaluates 32 Sturm
+// counts at once and shrinks the bracket 33-fold; lane 0 then runs the
+// inverse iteration and writes the results.
 __device__ void tridiag_lowest(const double* alpha, const double* beta, int n, double* theta_out, double* yout) {
+  const int lane = threadIdx.x & 31;
   double lo = 1e300, hi = -1e300;
   for (int i = 0; i < n; ++i) {
     double r = (i > 0 ? fabs(beta[i - 1]) : 0.0) + (i < n - 1 ? fabs(beta[i]) : 0.0);
     lo = fmin(lo, alpha[i] - r);
     hi = fmax(hi, alpha[i] + r);
   }
-  for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(alpha, beta, n, mid) >= 1) hi = mid; else lo = mid;
+  for (int round = 0; round < 40; ++round) {
+    const double w = hi - lo;
+    if (!(w > 4e-16 * fmax(fabs(lo), fabs(hi)))) break;
+    const double x = lo + w * (double)(lane + 1) / 33.0;
+    const unsigned mask = __ballot_sync(0xffffffffu, sturm_count(alpha, beta, n, x) >= 1);
+    const int first = mask ? __ffs(mask) - 1 : 32;  // smallest point above lambda_min
+    const double nhi = (first < 32) ? lo + w * (double)(first + 1) / 33.0 : hi;
+    const double nlo = (first > 0) ? lo + w * (double)first / 33.0 : lo;
+    if (nhi >= hi && nlo <= lo) break;
+    lo = nlo;
+    hi = nhi;
   }
+  if (lane != 0) return;
   const double theta = 0.5 * (lo + hi);
   // inverse iteration with partial pivoting (n <= 64)
   double y[64], z[64];
@@ -138,7 +150,7 @@ __device__ void tridiag_lowest(const double* alpha, const double* beta, int n, d
   int piv[64];
   for (int i = 0; i < n; ++i) y[i] = 1.0 / sqrt((double)n);
   const double scale = fmax(fabs(lo), fabs(hi)) + 1e-300;
-  for (int iter = 0; iter < 4; ++iter) {
+  for (int iter = 0; iter < 3; ++iter) {
     for (int i = 0; i < n; ++i) {
       dd[i] = alpha[i] - theta;
       du[i] = (i < n - 1) ? beta[i] : 0.0;
@@ -196,18 +208,31 @@ __device__ void tridiag_lowest(const double* alpha, const double* beta, int n, d
   for (int i = 0; i < n; ++i) yout[i] = sg * y[i];
 }
 
-// After step k: beta_k = ||w||, Ritz pair of T_{k+1}, stop decision (all on device).
+// After step k (one warp): alpha_k from the two Gram-Schmidt passes, beta_k =
+// ||w||, Ritz pair of T_{k+1} and the stop decision, all on the device. With
+// tol <= 0 (fixed depth) the Ritz solve runs only at the last step or on breakdown.
 __global__ void lz_step(double* S, int k, int depth, double tol) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0) return;
+  const int lane = threadIdx.x & 31;
   if (S[S_DONE] != 0.0) return;
+  const double a = S[S_H + k] + S[S_H2 + k];
   const double b = sqrt(fmax(S[S_TMP], 0.0));
-  S[S_BETA + k] = b;
+  __syncwarp();
+  if (lane == 0) {
+    S[S_ALPHA + k] = a;
+    S[S_BETA + k] = b;
+  }
+  __syncwarp();
+  const double prev = k > 0 ? S[S_BETA + k - 1] : 0.0;
+  const bool breakdown = b < 1e-14 * (fabs(a) + prev + 1e-300) || !isfinite(b);
+  if (tol <= 0.0 && k < depth - 1 && !breakdown) return;
   const int n = k + 1;
   double theta, y[64];
   tridiag_lowest(S + S_ALPHA, S + S_BETA, n, &theta, y);
+  if (lane != 0) return;
   const double resid = fabs(b * y[n - 1]);
   const double sc = fmax(fabs(theta), 1e-300);
-  const bool stop = resid < tol * sc || b < 1e-14 * sc || k == depth - 1 || !isfinite(theta) || !isfinite(b);
+  const bool stop = resid < tol * sc || b < 1e-14 * sc || breakdown || k == depth - 1 || !isfinite(theta);
   S[S_THETA] = theta;
   S[S_RESID] = resid;
   S[S_NK] = (double)n;
@@ -280,20 +305,16 @@ void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int 
   for (int k = 0; k < depth; ++k) {
     double* vk = B + (long)k * V;
     apply(vk, W);
-    multi_dot_g(ctx, vk, 1, V, W, S + S_ALPHA + k, nullptr, done);
-    multi_axpy<<<vgrid(V), LT, 0, s>>>(W, vk, S + S_ALPHA + k, 1, V, 1.0, done);
-    ctx->launches++;
-    if (k > 0) {
-      multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B + (long)(k - 1) * V, S + S_BETA + (k - 1), 1, V, 1.0, done);
-      ctx->launches++;
-    }
-    for (int pass = 0; pass < 2; ++pass) {
-      multi_dot_g(ctx, B, k + 1, V, W, S + S_H, nullptr, done);
-      multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H, k + 1, V, 1.0, done);
-      ctx->launches++;
-    }
+    // w -= sum_i <v_i, w> v_i over the whole basis, twice; the coefficient of
+    // v_k is alpha_k and those of v_{k-1} and older vectors take the place of
+    // the three-term recurrence (equal in exact arithmetic)
+    multi_dot_g(ctx, B, k + 1, V, W, S + S_H, nullptr, done);
+    multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H, k + 1, V, 1.0, done);
+    multi_dot_g(ctx, B, k + 1, V, W, S + S_H2, nullptr, done);
+    multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H2, k + 1, V, 1.0, done);
+    ctx->launches += 2;
     multi_dot_g(ctx, W, 1, V, W, S + S_TMP, nullptr, done);
-    lz_step<<<1, 1, 0, s>>>(S, k, depth, tol);
+    lz_step<<<1, 32, 0, s>>>(S, k, depth, tol);
     ctx->launches++;
     if (k + 1 < depth) {
       scale_by_norm<<<vgrid(V), LT, 0, s>>>(B + (long)(k + 1) * V, W, S + S_TMP, V, done);

@@ -444,7 +444,8 @@ double attn_state::local_step(int n) {
     tmpT.reserve(sizeof(double) * V);
     double* v = tmpT.as<double>();
     copy_f64(ctx, v, tensor(n), V);
-    const attn_dtype dt = cfg.matvec_dtype;
+    // nodes whose links are too small for the tensor-core tiles use FP64 matvecs
+    const attn_dtype dt = (cfg.matvec_dtype == ATTN_BF16 && tc_supported(h)) ? ATTN_BF16 : ATTN_F64;
     MatVec mv_lo = [&](const double* a, double* b) {
       if (dt == ATTN_BF16) h->apply_bf16(a, b); else h->apply_f64(a, b);
     };

@@ -78,22 +78,23 @@ def test_graph_eigsolve_equals_plain():
     attn.attn_move_centre(st, node)
     H = attn.attn_heff_build(st, node)
     x0 = attn.attn_node_get(st, node)
-    out = {}
-    for g in (0, 1):
-        cfg = attn.attn_get_config(ctx)
-        cfg.use_graphs = g
-        cfg.lanczos_tol = 0.0
-        cfg.matvec_dtype = attn.ATTN_BF16
-        cfg.refine_steps = 2
-        attn.attn_set_config(ctx, cfg)
-        t = dev(x0)
-        res = [attn.attn_eigsolve(H, t) for _ in range(2 if g else 1)]
-        if g:  # replays start from the previous result; compare the first one
-            t = dev(x0)
-            res = [attn.attn_eigsolve(H, t)]
-        out[g] = (res[-1][0], host(t))
-    assert abs(out[0][0] - out[1][0]) < 1e-12 * abs(out[0][0])
-    assert np.abs(out[0][1] - out[1][1]).max() < 1e-10
+    for dtype, tol in ((attn.ATTN_F64, 1e-12), (attn.ATTN_BF16, 1e-6)):
+        # FP64 matvecs are deterministic: graph replay must reproduce the plain solve;
+        # BF16 products split over CTAs meet by FP32 atomics (last-bit order effects)
+        out = {}
+        for g in (0, 1):
+            cfg = attn.attn_get_config(ctx)
+            cfg.use_graphs = g
+            cfg.lanczos_tol = 0.0
+            cfg.matvec_dtype = dtype
+            cfg.refine_steps = 2
+            attn.attn_set_config(ctx, cfg)
+            for _ in range(2 if g else 1):  # a second replay re-uses the captured graph
+                t = dev(x0)
+                th, _ = attn.attn_eigsolve(H, t)
+            out[g] = (th, host(t))
+        assert abs(out[0][0] - out[1][0]) < tol * abs(out[0][0])
+        assert np.abs(out[0][1] - out[1][1]).max() < 100 * tol
     attn.attn_heff_destroy(H)
     attn.attn_state_destroy(st)
     attn.attn_model_destroy(mod)
