@@ -17,13 +17,18 @@
 // D1 and D2 for each slice (4 x 128 columns). The MMA order is
 //   S1(r, 0), S1(r, 1), S2(r, 0), S2(r, 1), S1(r+1, 0), ...
 // so that converting slice 0 overlaps stage 1 of slice 1 and converting slice 1
-// overlaps stage 2 of slice 0. Operator tiles stream through one ring of 16 KB
+// overlaps stage 2 of slice 0; each 64-column half of Z^T is handed to stage 2
+// as soon as it is packed. At N = 128 one MMA (K = 16) takes 64 cycles, which
+// one issuing thread cannot sustain between its waits and commits: the two
+// stages are issued by two threads, with descriptors precomputed and each K
+// block unrolled. Operator tiles stream through one ring of 16 KB
 // K-block stages in consumption order (B_r, A_r, B_{r+1}, ...). A slice pair's
 // product list may be split over several CTAs (`rsplit`, chosen by an
 // autotuner at the first application) whose partial Y_s meet by FP32 atomics.
 //
 // Warp roles (640 threads): warp 0 = TMA producer, warp 1 = TMEM allocation
-// and MMA issue, warps 4-19 = conversion and epilogue, eight per slice in two
+// and stage-1 MMA issue, warp 2 = stage-2 MMA issue, warps 4-19 = conversion
+// and epilogue, eight per slice in two
 // column halves (warp w reads TMEM lanes 32*(w%4) .. +31). Internal
 // (single-link) operators enter as products with an identity partner;
 // three-link products go through the FP64 path. Every mbarrier wait is
@@ -89,8 +94,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // ------------------------------------------------------------------ kernel
 __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_constant__ TcMaps maps, TcParams prm) {
   extern __shared__ uint8_t smem_raw[];
-  // 1024-aligned regions: X of both slices, operator ring, barriers. X K block kb
-  // holds 256 rows: slice 0 in rows 0..P-1, slice 1 in rows 128..127+P.
+  // 1024-aligned regions: X of both slices (K block kb of slice u at
+  // 32 KB kb + 16 KB u), operator ring, barriers.
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
@@ -101,10 +106,12 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     XFULL = 0,
     FULL = 1,
     EMPTY = 1 + kStages,
-    D1FULL = 1 + 2 * kStages,  // stage 1 of both slices done
-    ZFULL = 2 + 2 * kStages,   // [slice][half]: that half of Z^T packed in TMEM
-    D2FULL = 6 + 2 * kStages,
-    NBAR = 7 + 2 * kStages
+    D1FULL = 1 + 2 * kStages,  // [slice]: stage 1 done
+    ZFULL = 3 + 2 * kStages,   // [slice][half]: that half of Z^T packed in TMEM
+    S2DONE = 7 + 2 * kStages,  // [slice]: stage 2 done, D1 free for the next product
+    D2FULL = 9 + 2 * kStages,
+    S1END = 10 + 2 * kStages,  // every stage-1 MMA complete (TMEM may be freed)
+    NBAR = 11 + 2 * kStages
   };
   uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + (sBar - base));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBAR);
@@ -132,24 +139,17 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
       mbar_init(bar(FULL + i), 1);
       mbar_init(bar(EMPTY + i), 1);
     }
-    mbar_init(bar(D1FULL), 1);
+    for (int u = 0; u < 2; ++u) {
+      mbar_init(bar(D1FULL + u), 1);
+      mbar_init(bar(S2DONE + u), 1);
+    }
     for (int i = 0; i < 4; ++i) mbar_init(bar(ZFULL + i), kHalfThreads);
     mbar_init(bar(D2FULL), 1);
+    mbar_init(bar(S1END), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (P < 128) {
-    // rows P..127 of each slice's X block are not loaded; zero them so that the
-    // unused stage-1 columns hold finite values
-    const int nkb = (Q + 63) / 64;
-    for (int e = threadIdx.x; e < nkb * 2 * (128 - P) * 8; e += blockDim.x) {
-      const int c16 = e & 7, row = (e >> 3) % (128 - P), rest = (e >> 3) / (128 - P);
-      const int u = rest & 1, kblk = rest >> 1;
-      *reinterpret_cast<uint4*>(gbase + kblk * 2 * kTileBytes / 2 + u * (kTileBytes / 2) + (P + row) * 128 + c16 * 16) =
-          make_uint4(0, 0, 0, 0);
-    }
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kTmemCols));
@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
   fence_after();
   const uint32_t tmem = *tmem_slot;
   // TMEM: D1 of slice u in columns 128u .. 128u+P-1 (Z^T packed in place), D2 of slice u at 256 + 128u
+  auto tD1 = [&](int u) { return tmem + 128u * (uint32_t)u; };
   auto tD2 = [&](int u) { return tmem + 256u + 128u * (uint32_t)u; };
   const int nkbQ = (Q + 63) / 64, nkbP = (P + 63) / 64;
   const CUtensorMap* mX = &maps.x[kind];
@@ -173,21 +174,23 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
       for (int kb = 0; kb < nkbQ; ++kb)
         tma_load_3d(sX + kb * kTileBytes + u * (kTileBytes / 2), mX, 64 * kb, 0, s0 + u, bar(XFULL));
     int issued = 0;
+    int st = 0;       // ring stage of the next load
+    uint32_t ph = 0;  // parity of that stage's current fill
     bool ok = true;
     for (int r = 0; ok && r < R; ++r) {
       for (int half = 0; ok && half < 2; ++half) {
         const CUtensorMap* mp = half == 0 ? mB : mA;
         const int nkb = half == 0 ? nkbQ : nkbP;
         for (int kb = 0; kb < nkb; ++kb) {
-          const int st = issued % kStages;
-          if (issued >= kStages &&
-              !mbar_wait(bar(EMPTY + st), ((issued / kStages) - 1) & 1, prm.err, 11, abort_flag)) {
+          // the stage's previous contents (fill ph - 1) must have been consumed
+          if (issued >= kStages && !mbar_wait(bar(EMPTY + st), ph ^ 1u, prm.err, 11, abort_flag)) {
             ok = false;
             break;
           }
           mbar_expect_tx(bar(FULL + st), (uint32_t)kKBlockBytes);
           tma_load_3d(sRing + st * kKBlockBytes, mp, 64 * kb, 0, r_begin + r, bar(FULL + st));
           ++issued;
+          if (++st == kStages) { st = 0; ph ^= 1u; }
         }
       }
     }
@@ -200,51 +203,88 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
       long long t0 = clock64();
       while (!mbar_try_wait(bar(FULL + q % kStages), (q / kStages) & 1) && clock64() - t0 < kWaitCycles) {}
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer. Stage 1 covers both slices in one N = 128 + P instruction
-    // stream (N = P for a lone slice); stage 2 runs per slice with N = P.
-    const uint32_t id1 = idesc_bf16(128, nsl == 2 ? 128 + P : P);
-    const uint32_t id2 = idesc_bf16(128, P);
-    bool ok = mbar_wait(bar(XFULL), 0, prm.err, 31, abort_flag);
-    int pos = 0;
-    for (int r = 0; ok && r < R; ++r) {
-      const int posB = pos, posA = pos + nkbQ;
-      pos += nkbQ + nkbP;
-      // stage 1: D1 = B_r [X_0; X_1]^T. D1 still holds Z of product r-1, but every
-      // stage-2 MMA reading it was issued earlier and MMAs of one thread run in order.
-      for (int kb = 0; kb < nkbQ; ++kb) {
-        const int q = posB + kb, st = q % kStages;
-        if (!mbar_wait(bar(FULL + st), (q / kStages) & 1, prm.err, 32, abort_flag)) { ok = false; break; }
-        fence_after();
-        const uint32_t aB = sRing + st * kKBlockBytes, aX = sX + kb * kTileBytes;
-        for (int k4 = 0; k4 < 4 && kb * 4 + k4 < Q / 16; ++k4)
-          mma_bf16(tmem, sw128_desc(aB + 32 * k4), sw128_desc(aX + 32 * k4), id1, (kb > 0 || k4 > 0));
-        mma_commit(bar(EMPTY + st));
-      }
-      if (!ok) break;
-      mma_commit(bar(D1FULL));
-      // stage 2 per slice: D2_u += Z_u^T A_r^T, Z_u read from TMEM half by half
-      for (int u = 0; ok && u < nsl; ++u) {
-        for (int kb = 0; kb < nkbP; ++kb) {
-          const int q = posA + kb, st = q % kStages;
-          if (!mbar_wait(bar(ZFULL + 2 * u + kb), r & 1, prm.err, 34, abort_flag)) { ok = false; break; }
-          if (u == 0 && !mbar_wait(bar(FULL + st), (q / kStages) & 1, prm.err, 33, abort_flag)) { ok = false; break; }
+  } else if ((warp == 1 || warp == 2) && lane == 0) {
+    // ---- MMA issue, split over two threads on different SM sub-partitions: a
+    // single thread cannot issue N = 128 MMAs (64 cycles each) back to back once
+    // waits and commits are interleaved. Warp 1 issues stage 1, warp 2 stage 2;
+    // the pipe sees S1(r,0), S1(r,1), S2(r,0), S2(r,1), S1(r+1,0), ...
+    const uint32_t id = idesc_bf16(128, P);  // both stages: M = 128 TMEM lanes, N = P
+    const int nk16Q = Q / 16, nk16P = P / 16;
+    const uint64_t dRing0 = sw128_desc(sRing);  // ring stage st: + st * (kKBlockBytes >> 4)
+    const uint32_t barFull = bar(FULL), barEmpty = bar(EMPTY);
+    int st = 0;        // ring stage of the product's first K block
+    uint32_t ph = 0;   // its phase parity
+    auto advance = [&](int n) {
+      for (int i = 0; i < n; ++i)
+        if (++st == kStages) { st = 0; ph ^= 1u; }
+    };
+    if (warp == 1) {
+      const uint64_t dX0 = sw128_desc(sX);  // X block kb of slice u: + (32 KB kb + 16 KB u) >> 4
+      bool ok = mbar_wait(bar(XFULL), 0, prm.err, 31, abort_flag);
+      for (int r = 0; ok && r < R; ++r) {
+        // stage 1 per slice: D1_u = B_r X_u^T (the B_r blocks serve both slices)
+        for (int u = 0; ok && u < nsl; ++u) {
+          // D1_u holds Z_u of product r-1 until its stage 2 has completed
+          if (r > 0 && !mbar_wait(bar(S2DONE + u), (r - 1) & 1, prm.err, 35, abort_flag)) { ok = false; break; }
           fence_after();
-          const uint32_t aA = sRing + st * kKBlockBytes;
-          const uint32_t aZ = tmem + 128u * (uint32_t)u + 64u * (uint32_t)kb;
-          for (int k4 = 0; k4 < 4; ++k4) {
-            const int kk = kb * 4 + k4;  // K step over i' (16 wide, 8 packed TMEM columns)
-            if (kk < P / 16)
-              mma_bf16_ts(tD2(u), aZ + 8 * k4, sw128_desc(aA + 32 * k4), id2, (r > 0 || kk > 0) ? 1u : 0u);
+          int s1 = st;
+          uint32_t p1 = ph;
+          for (int kb = 0; kb < nkbQ; ++kb) {
+            if (u == 0 && !mbar_wait(barFull + 8 * s1, p1, prm.err, 32, abort_flag)) { ok = false; break; }
+            const uint64_t dB = dRing0 + (uint64_t)(s1 * (kKBlockBytes >> 4));
+            const uint64_t dX = dX0 + (uint64_t)((kb * kTileBytes + u * (kTileBytes / 2)) >> 4);
+            const int n4 = nk16Q - 4 * kb;
+            if (n4 >= 4) {
+              mma4_ss(tD1(u), dB, dX, id, kb > 0 ? 1u : 0u);
+            } else {
+              for (int k4 = 0; k4 < n4; ++k4)
+                mma_bf16(tD1(u), dB + 2 * k4, dX + 2 * k4, id, (kb > 0 || k4 > 0) ? 1u : 0u);
+            }
+            if (u == nsl - 1) mma_commit(barEmpty + 8 * s1);
+            if (++s1 == kStages) { s1 = 0; p1 ^= 1u; }
           }
-          if (u == nsl - 1) mma_commit(bar(EMPTY + st));
+          if (!ok) break;
+          mma_commit(bar(D1FULL + u));
         }
+        advance(nkbQ + nkbP);
       }
+      mma_commit(bar(S1END));
+      long long t0 = clock64();
+      while (!mbar_try_wait(bar(S1END), 0) && clock64() - t0 < kWaitCycles) {}
+    } else {
+      bool ok = true;
+      for (int r = 0; ok && r < R; ++r) {
+        advance(nkbQ);
+        // stage 2 per slice: D2_u += Z_u^T A_r^T, Z_u read from TMEM half by half
+        for (int u = 0; ok && u < nsl; ++u) {
+          int s2 = st;
+          uint32_t p2 = ph;
+          for (int kb = 0; kb < nkbP; ++kb) {
+            if (!mbar_wait(bar(ZFULL + 2 * u + kb), r & 1, prm.err, 34, abort_flag)) { ok = false; break; }
+            if (u == 0 && !mbar_wait(barFull + 8 * s2, p2, prm.err, 33, abort_flag)) { ok = false; break; }
+            fence_after();  // Z was written by tcgen05.st in other threads
+            const uint64_t dA = dRing0 + (uint64_t)(s2 * (kKBlockBytes >> 4));
+            const uint32_t aZ = tD1(u) + 64u * (uint32_t)kb;
+            const int n4 = nk16P - 4 * kb;
+            if (n4 >= 4) {
+              mma4_ts(tD2(u), aZ, dA, id, (r > 0 || kb > 0) ? 1u : 0u);
+            } else {
+              for (int k4 = 0; k4 < n4; ++k4)
+                mma_bf16_ts(tD2(u), aZ + 8 * k4, dA + 2 * k4, id, (r > 0 || kb > 0 || k4 > 0) ? 1u : 0u);
+            }
+            if (u == nsl - 1) mma_commit(barEmpty + 8 * s2);
+            if (++s2 == kStages) { s2 = 0; p2 ^= 1u; }
+          }
+          if (!ok) break;
+          mma_commit(bar(S2DONE + u));
+        }
+        advance(nkbP);
+      }
+      mma_commit(bar(D2FULL));
+      // every MMA this thread issued must finish before TMEM can be freed
+      long long t0 = clock64();
+      while (!mbar_try_wait(bar(D2FULL), 0) && clock64() - t0 < kWaitCycles) {}
     }
-    mma_commit(bar(D2FULL));
-    // every MMA this thread issued must finish before TMEM can be freed
-    long long t0 = clock64();
-    while (!mbar_try_wait(bar(D2FULL), 0) && clock64() - t0 < kWaitCycles) {}
   } else if (warp >= 4) {
     // ---- conversion D1 -> packed BF16 Z^T and the epilogue. Slice u has warps
     // 4+8u .. 11+8u; warps of half hh own the 64 columns from 64 hh of the slice's
@@ -255,11 +295,11 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     const int j = q4 * 32 + lane;  // TMEM lane == row j of D1 and of D2 = Y^T
     const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
     const int c0 = 64 * hh;
-    const uint32_t tz = tmem + lane_off + 128u * (uint32_t)u + (uint32_t)c0;
+    const uint32_t tz = tD1(u) + lane_off + (uint32_t)c0;
     bool ok = u < nsl && c0 < P;
     for (int r = 0; ok && r < R; ++r) {
       // warp-uniform: the TMEM accesses below are .sync.aligned
-      if (!__all_sync(0xffffffffu, mbar_wait(bar(D1FULL), r & 1, prm.err, 41, abort_flag))) { ok = false; break; }
+      if (!__all_sync(0xffffffffu, mbar_wait(bar(D1FULL + u), r & 1, prm.err, 41, abort_flag))) { ok = false; break; }
       fence_after();
       uint32_t w[32];  // packed BF16 pairs of this thread's 64 columns
 #pragma unroll

@@ -39,6 +39,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 // Bounded wait: false (and `code` recorded in *err) after ~kWaitCycles or once another thread aborted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;  // fast path: no clock read when already complete
   long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
@@ -58,15 +59,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
 }
-// K-major operand tile with the 128-byte swizzle (8-row groups of 1024 bytes).
+// K-major operand tile with the 128-byte swizzle (8-row groups of 1024 bytes):
+// start address >> 4 in bits 0-13, leading byte offset 16 (unused for this
+// layout), stride byte offset 1024 between 8-row groups, descriptor version 1,
+// swizzle mode 128B. Advancing one K step of 16 BF16 elements (32 bytes) adds 2.
+constexpr uint64_t kSw128DescHi = ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
+                                  ((uint64_t)2 << 61);
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
+  return kSw128DescHi | (uint64_t)((saddr & 0x3FFFFu) >> 4);
 }
 // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major.
 __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
@@ -120,6 +120,14 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&w)[32
       : "r"(taddr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]), "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15]), "r"(w[16]), "r"(w[17]), "r"(w[18]), "r"(w[19]), "r"(w[20]), "r"(w[21]), "r"(w[22]), "r"(w[23]), "r"(w[24]), "r"(w[25]), "r"(w[26]), "r"(w[27]), "r"(w[28]), "r"(w[29]), "r"(w[30]), "r"(w[31])
       : "memory");
 }
+// The four K = 16 steps of one 64-wide K block, descriptors advanced in place
+// (single-thread issue cost matters: an MMA of N = 128 takes only 64 cycles).
+__device__ __forceinline__ void mma4_ss(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc_first) {
+  mma_bf16(d, da, db, idesc, acc_first);
+  mma_bf16(d, da + 2, db + 2, idesc, 1u);
+  mma_bf16(d, da + 4, db + 4, idesc, 1u);
+  mma_bf16(d, da + 6, db + 6, idesc, 1u);
+}
 // kind::f16 MMA whose A operand (M x 16, BF16 pairs packed into 32-bit columns,
 // one row per lane) is read from tensor memory instead of shared memory.
 __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
@@ -129,6 +137,13 @@ __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, ui
           d_tmem),
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
+}
+// TS form of mma4_ss: A advances 8 TMEM columns (16 packed BF16) per K step.
+__device__ __forceinline__ void mma4_ts(uint32_t d, uint32_t a_tmem, uint64_t db, uint32_t idesc, uint32_t acc_first) {
+  mma_bf16_ts(d, a_tmem, db, idesc, acc_first);
+  mma_bf16_ts(d, a_tmem + 8, db + 2, idesc, 1u);
+  mma_bf16_ts(d, a_tmem + 16, db + 4, idesc, 1u);
+  mma_bf16_ts(d, a_tmem + 24, db + 6, idesc, 1u);
 }
 // Barrier over a subset of the block's warps (id 1..15; id 0 is __syncthreads).
 __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
