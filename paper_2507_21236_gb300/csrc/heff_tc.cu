@@ -63,7 +63,7 @@ namespace {
 using namespace tc;
 
 constexpr int kThreads = 640;         // 4 role warps + 16 conversion/epilogue warps
-constexpr int kHalfThreads = 128;     // conversion threads per slice half (Z-full arrivals)
+constexpr int kHalfWarps = 4;         // conversion warps per slice half (one Z-full arrival each)
 constexpr int kTileBytes = 128 * 128 * 2;  // one 128 x 128 BF16 tile (two 64-wide K blocks)
 constexpr int kKBlockBytes = 128 * 128;    // 128 rows x 128 bytes
 constexpr int kStages = 10;                // operator ring depth (K blocks)
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
       mbar_init(bar(D1FULL + u), 1);
       mbar_init(bar(S2DONE + u), 1);
     }
-    for (int i = 0; i < 4; ++i) mbar_init(bar(ZFULL + i), kHalfThreads);
+    for (int i = 0; i < 4; ++i) mbar_init(bar(ZFULL + i), kHalfWarps);
     mbar_init(bar(D2FULL), 1);
     mbar_init(bar(S1END), 1);
     *abort_flag = 0;
@@ -311,7 +311,9 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
       }
       tmem_st32(tz, w);
       fence_before();
-      mbar_arrive(bar(ZFULL + 2 * u + hh));
+      // one arrival per warp: 256 arrivals on one barrier would serialise on its word
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(ZFULL + 2 * u + hh));
     }
     if (ok && R > 0 && __all_sync(0xffffffffu, mbar_wait(bar(D2FULL), 0, prm.err, 43, abort_flag))) {
       fence_after();
