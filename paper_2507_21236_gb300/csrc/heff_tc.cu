@@ -345,36 +345,57 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
 
 // ------------------------------------------------------------ prep kernels
 // x (fp64 [m0][m1][m2]) -> bf16 slice-major copies for the three pair kinds:
-// X01[c][a][b], X02[b][a][c], X12[a][b][c].
-__global__ void prep_x_kernel(const double* x, int m0, int m1, int m2, __nv_bfloat16* x01, __nv_bfloat16* x02,
-                              __nv_bfloat16* x12) {
-  const long V = (long)m0 * m1 * m2;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < V; e += (long)gridDim.x * blockDim.x) {
-    const int c = e % m2;
-    const long t = e / m2;
-    const int b = t % m1, a = t / m1;
-    const __nv_bfloat16 v = __double2bfloat16(x[e]);
-    if (x01) x01[((long)c * m0 + a) * m1 + b] = v;
-    if (x02) x02[((long)b * m0 + a) * m2 + c] = v;
-    if (x12) x12[e] = v;
+// X01[c][a][b], X02[b][a][c], X12[a][b][c]. One block handles a 32 x 32 tile of
+// the (b, c) plane of one a: X02 and X12 rows are contiguous in c like x, and
+// the b <-> c transpose for X01 goes through shared memory, so every global
+// access is coalesced.
+constexpr int kTile = 32;
+
+__global__ void prep_x_kernel(const double* __restrict__ x, int m0, int m1, int m2, __nv_bfloat16* x01,
+                              __nv_bfloat16* x02, __nv_bfloat16* x12) {
+  __shared__ __nv_bfloat16 t[kTile][kTile + 2];
+  const int a = blockIdx.z, b0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
+  for (int bb = threadIdx.y; bb < kTile; bb += blockDim.y) {
+    const int b = b0 + bb, c = c0 + threadIdx.x;
+    if (b < m1 && c < m2) {
+      const __nv_bfloat16 v = __double2bfloat16(x[((long)a * m1 + b) * m2 + c]);
+      t[bb][threadIdx.x] = v;
+      if (x02) x02[((long)b * m0 + a) * m2 + c] = v;
+      if (x12) x12[((long)a * m1 + b) * m2 + c] = v;
+    }
+  }
+  if (!x01) return;
+  __syncthreads();
+  for (int cc = threadIdx.y; cc < kTile; cc += blockDim.y) {
+    const int c = c0 + cc, b = b0 + threadIdx.x;
+    if (b < m1 && c < m2) x01[((long)c * m0 + a) * m1 + b] = t[threadIdx.x][cc];
   }
 }
 
-// y = Y01^T + Y02^T + Y12 (fp32 -> fp64)
-__global__ void combine_kernel(double* y, int m0, int m1, int m2, const float* y01, const float* y02,
+// y = Y01^T + Y02^T + Y12 (fp32 -> fp64), the same tiling as prep_x_kernel.
+__global__ void combine_kernel(double* __restrict__ y, int m0, int m1, int m2, const float* y01, const float* y02,
                                const float* y12) {
-  const long V = (long)m0 * m1 * m2;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < V; e += (long)gridDim.x * blockDim.x) {
-    const int c = e % m2;
-    const long t = e / m2;
-    const int b = t % m1, a = t / m1;
-    double v = 0.0;
-    if (y01) v += (double)y01[((long)c * m0 + a) * m1 + b];
-    if (y02) v += (double)y02[((long)b * m0 + a) * m2 + c];
-    if (y12) v += (double)y12[e];
-    y[e] = v;
+  __shared__ float t[kTile][kTile + 1];
+  const int a = blockIdx.z, b0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
+  if (y01) {
+    for (int cc = threadIdx.y; cc < kTile; cc += blockDim.y) {
+      const int c = c0 + cc, b = b0 + threadIdx.x;
+      if (b < m1 && c < m2) t[threadIdx.x][cc] = y01[((long)c * m0 + a) * m1 + b];
+    }
+    __syncthreads();
+  }
+  for (int bb = threadIdx.y; bb < kTile; bb += blockDim.y) {
+    const int b = b0 + bb, c = c0 + threadIdx.x;
+    if (b < m1 && c < m2) {
+      double v = y01 ? (double)t[bb][threadIdx.x] : 0.0;
+      if (y02) v += (double)y02[((long)b * m0 + a) * m2 + c];
+      if (y12) v += (double)y12[((long)a * m1 + b) * m2 + c];
+      y[((long)a * m1 + b) * m2 + c] = v;
+    }
   }
 }
+
+dim3 tile_grid(const int* m) { return dim3((m[2] + kTile - 1) / kTile, (m[1] + kTile - 1) / kTile, m[0]); }
 
 __global__ void to_bf16_kernel(__nv_bfloat16* dst, const double* src, long n) {
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
@@ -534,7 +555,7 @@ void attn_heff::apply_bf16(const double* x, double* y) {
   TcState* t = static_cast<TcState*>(tc);
   cudaStream_t st = ctx->stream;
   // the kind buffers are indexed by pair kind k (0,1,2); kinds with no products pass null
-  prep_x_kernel<<<vgrid(V), 256, 0, st>>>(x, m[0], m[1], m[2], t->R[0] ? t->x[0].as<__nv_bfloat16>() : nullptr,
+  prep_x_kernel<<<tile_grid(m), dim3(kTile, 8), 0, st>>>(x, m[0], m[1], m[2], t->R[0] ? t->x[0].as<__nv_bfloat16>() : nullptr,
                                           t->R[1] ? t->x[1].as<__nv_bfloat16>() : nullptr,
                                           t->R[2] ? t->x[2].as<__nv_bfloat16>() : nullptr);
   ctx->launches++;
@@ -587,7 +608,7 @@ void attn_heff::apply_bf16(const double* x, double* y) {
     ctx->prof_end(0, fl);
     ctx->launches++;
   }
-  combine_kernel<<<vgrid(V), 256, 0, st>>>(y, m[0], m[1], m[2], t->R[0] ? t->y[0].as<float>() : nullptr,
+  combine_kernel<<<tile_grid(m), dim3(kTile, 8), 0, st>>>(y, m[0], m[1], m[2], t->R[0] ? t->y[0].as<float>() : nullptr,
                                            t->R[1] ? t->y[1].as<float>() : nullptr,
                                            t->R[2] ? t->y[2].as<float>() : nullptr);
   ctx->launches++;

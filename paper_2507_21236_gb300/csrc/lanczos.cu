@@ -2,7 +2,8 @@
 // eigenproblem is solved with Lanczos; the matrix-vector product is H_eff).
 //
 // Krylov recurrence from the current centre tensor, full reorthogonalisation
-// (classical Gram-Schmidt against the whole basis, twice), and the lowest
+// (classical Gram-Schmidt against the whole basis, twice, as three fused
+// streaming passes), and the lowest
 // eigenpair of the tridiagonal projection computed on the device: bisection
 // with Sturm counts for the eigenvalue, inverse iteration (tridiagonal
 // Gaussian elimination with partial pivoting) for the eigenvector. Stops when
@@ -84,6 +85,128 @@ __global__ void multi_axpy(double* w, const double* basis, const double* coef, i
     for (int i = 0; i < nvec; ++i) v = fma(-sign * coef[i], basis[(long)i * V + e], v);
     w[e] = v;
   }
+}
+
+// ---- fused classical Gram-Schmidt passes (up to kFusedMax basis vectors).
+// One CGS2 step as three streaming passes over the basis instead of five:
+//   (A) h_i = <v_i, w>;  (B) w -= sum h_i v_i and h2_i = <v_i, w>;
+//   (C) w -= sum h2_i v_i and ||w||^2.
+// Each pass reads every basis vector once; block partials are summed in a fixed
+// order by multi_dot_reduce, so results are deterministic. The kernels are
+// instantiated for NV vectors at most with U elements per thread and step
+// (fewer vectors -> more elements), so that every thread keeps NV * U loads in
+// flight: a streaming pass over HBM needs about 40 KB outstanding per SM.
+constexpr int kFusedMax = 24;
+
+// Sum the per-thread values acc[0..n) over the block and write them to out[0..n).
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&acc)[NV], int n, double* out) {
+  __shared__ double sh[LT / 32][NV];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    if (i < n) {
+      const double s = warp_sum(acc[i]);
+      if (lane == 0) sh[warp][i] = s;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    double t = 0.0;
+    for (int q = 0; q < LT / 32; ++q) t += sh[q][threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+}
+
+// (A) part[b][i] = block b's share of <basis_i, w>
+template <int NV, int U>
+__global__ void __launch_bounds__(LT) cgs_dot(const double* __restrict__ basis, int n, long V,
+                                              const double* __restrict__ w, double* part, const double* done) {
+  if (done && *done != 0.0) return;
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  const long stride = (long)gridDim.x * LT;
+  for (long e0 = blockIdx.x * (long)LT + threadIdx.x; e0 < V; e0 += stride * U) {
+    double we[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) we[u] = (e0 + u * stride < V) ? w[e0 + u * stride] : 0.0;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (i < n) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e0 + u * stride < V) acc[i] = fma(basis[(long)i * V + e0 + u * stride], we[u], acc[i]);
+      }
+  }
+  block_sum_store<NV>(acc, n, part + (long)blockIdx.x * n);
+}
+
+// (B) w -= sum_i h_i basis_i, then part[b][i] = block share of <basis_i, w_new>
+template <int NV, int U>
+__global__ void __launch_bounds__(LT) cgs_axpy_dot(double* __restrict__ w, const double* __restrict__ basis,
+                                                   const double* h, int n, long V, double* part, const double* done) {
+  if (done && *done != 0.0) return;
+  __shared__ double c[NV];
+  if (threadIdx.x < NV) c[threadIdx.x] = threadIdx.x < n ? h[threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  const long stride = (long)gridDim.x * LT;
+  for (long e0 = blockIdx.x * (long)LT + threadIdx.x; e0 < V; e0 += stride * U) {
+    double b[U][NV], v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long e = e0 + u * stride;
+      v[u] = e < V ? w[e] : 0.0;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) b[u][i] = (i < n && e < V) ? basis[(long)i * V + e] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (i < n) v[u] = fma(-c[i], b[u][i], v[u]);
+      const long e = e0 + u * stride;
+      if (e < V) w[e] = v[u];
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (i < n) acc[i] = fma(b[u][i], v[u], acc[i]);
+    }
+  }
+  block_sum_store<NV>(acc, n, part + (long)blockIdx.x * n);
+}
+
+// (C) w -= sum_i h_i basis_i, then part[b] = block share of ||w_new||^2
+template <int NV, int U>
+__global__ void __launch_bounds__(LT) cgs_axpy_norm(double* __restrict__ w, const double* __restrict__ basis,
+                                                    const double* h, int n, long V, double* part, const double* done) {
+  if (done && *done != 0.0) return;
+  __shared__ double c[NV];
+  if (threadIdx.x < NV) c[threadIdx.x] = threadIdx.x < n ? h[threadIdx.x] : 0.0;
+  __syncthreads();
+  double acc[1] = {0.0};
+  const long stride = (long)gridDim.x * LT;
+  for (long e0 = blockIdx.x * (long)LT + threadIdx.x; e0 < V; e0 += stride * U) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = (e0 + u * stride < V) ? w[e0 + u * stride] : 0.0;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (i < n) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (e0 + u * stride < V) v[u] = fma(-c[i], basis[(long)i * V + e0 + u * stride], v[u]);
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (e0 + u * stride < V) {
+        w[e0 + u * stride] = v[u];
+        acc[0] = fma(v[u], v[u], acc[0]);
+      }
+  }
+  block_sum_store<1>(acc, 1, part + blockIdx.x);
 }
 
 // out = sum_{i < n} coef[i] * basis_i with n = nvec, or (int)*nvec_dev if given
@@ -252,6 +375,39 @@ __global__ void lz_init(double* S) {
 
 inline int vgrid(long V) { return (int)std::max<long>(1, std::min<long>((V + LT - 1) / LT, LB)); }
 
+template <int NV, int U>
+void cgs2_launch(cudaStream_t s, const double* B, double* W, double* S, int n, long V, int nb, double* part,
+                 const double* done) {
+  cgs_dot<NV, U><<<nb, LT, 0, s>>>(B, n, V, W, part, done);
+  multi_dot_reduce<<<n, LT, 0, s>>>(part, nb, n, S + S_H, nullptr, done);
+  cgs_axpy_dot<NV, U><<<nb, LT, 0, s>>>(W, B, S + S_H, n, V, part, done);
+  multi_dot_reduce<<<n, LT, 0, s>>>(part, nb, n, S + S_H2, nullptr, done);
+  cgs_axpy_norm<NV, U><<<nb, LT, 0, s>>>(W, B, S + S_H2, n, V, part, done);
+  multi_dot_reduce<<<1, LT, 0, s>>>(part, nb, 1, S + S_TMP, nullptr, done);
+}
+
+// One CGS2 step against n <= kFusedMax basis vectors (six launches).
+void cgs2_fused(cudaStream_t s, const double* B, double* W, double* S, int n, long V, int nb, double* part,
+                const double* done) {
+  if (n <= 4) cgs2_launch<4, 4>(s, B, W, S, n, V, nb, part, done);
+  else if (n <= 8) cgs2_launch<8, 2>(s, B, W, S, n, V, nb, part, done);
+  else if (n <= 12) cgs2_launch<12, 2>(s, B, W, S, n, V, nb, part, done);
+  else if (n <= 16) cgs2_launch<16, 1>(s, B, W, S, n, V, nb, part, done);
+  else cgs2_launch<24, 1>(s, B, W, S, n, V, nb, part, done);
+}
+
+// Blocks for the fused streaming passes: enough resident warps on every SM to
+// keep HBM busy, never more blocks than elements / LT.
+int fused_grid(long V) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    ATTN_CHECK_CUDA(cudaGetDevice(&dev));
+    ATTN_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return (int)std::max<long>(1, std::min<long>((V + LT - 1) / LT, 4L * sms));
+}
+
 void multi_dot_g(attn_ctx* ctx, const double* basis, int nvec, long V, const double* w, double* out, double* accum,
                  const double* done) {
   const int nb = vgrid(V);
@@ -308,12 +464,20 @@ void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int 
     // w -= sum_i <v_i, w> v_i over the whole basis, twice; the coefficient of
     // v_k is alpha_k and those of v_{k-1} and older vectors take the place of
     // the three-term recurrence (equal in exact arithmetic)
-    multi_dot_g(ctx, B, k + 1, V, W, S + S_H, nullptr, done);
-    multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H, k + 1, V, 1.0, done);
-    multi_dot_g(ctx, B, k + 1, V, W, S + S_H2, nullptr, done);
-    multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H2, k + 1, V, 1.0, done);
-    ctx->launches += 2;
-    multi_dot_g(ctx, W, 1, V, W, S + S_TMP, nullptr, done);
+    const int n = k + 1;
+    if (n <= kFusedMax) {
+      const int nb = fused_grid(V);
+      ctx->partials.reserve(sizeof(double) * (size_t)nb * n);
+      cgs2_fused(s, B, W, S, n, V, nb, ctx->partials.as<double>(), done);
+      ctx->launches += 6;
+    } else {
+      multi_dot_g(ctx, B, n, V, W, S + S_H, nullptr, done);
+      multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H, n, V, 1.0, done);
+      multi_dot_g(ctx, B, n, V, W, S + S_H2, nullptr, done);
+      multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H2, n, V, 1.0, done);
+      ctx->launches += 2;
+      multi_dot_g(ctx, W, 1, V, W, S + S_TMP, nullptr, done);
+    }
     lz_step<<<1, 32, 0, s>>>(S, k, depth, tol);
     ctx->launches++;
     if (k + 1 < depth) {
