@@ -19,7 +19,9 @@ is single-GPU; no collective on the data path).
 bounded sample (a subset of the node's products), scaled to matvecs/s.
 """
 import argparse
+import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -38,6 +40,33 @@ WORKLOAD = "tfim32x32_m128_top_node_lanczos"
 
 def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+KERNEL_PROFILE = os.path.join(ROOT, "profiles", "sandwich_tc_kernel_tfim32x32_m128.md")
+
+
+def kernel_source_sha():
+    """SHA-256 of the sandwich kernel's source section: the code an ncu capture measured."""
+    with open(os.path.join(ROOT, "paper_2507_21236_gb300", "csrc", "heff_tc.cu")) as f:
+        src = f.read()
+    a = src.index("// ------------------------------------------------------------------ kernel")
+    b = src.index("// ------------------------------------------------------------ prep kernels")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) per launch from the committed ncu summary of the
+    sandwich kernel, or None when the kernel's source has changed since the capture."""
+    try:
+        with open(KERNEL_PROFILE) as f:
+            text = f.read()
+    except OSError:
+        return None
+    sha = re.search(r"kernel source sha256: `?([0-9a-f]{64})", text)
+    traffic = re.search(r"traffic per launch: `?([0-9]+) bytes", text)
+    if not sha or not traffic or sha.group(1) != kernel_source_sha():
+        return None
+    return int(traffic.group(1))
 
 
 def measured_peaks():
@@ -374,7 +403,7 @@ def main():
     achieved = (k_fl / k_n) / ((k_ms / k_n) / 1000.0) / 1e12 if k_n else None
     peak = peaks["bf16_tflops_sustained"]
     roof = {"bound": "tensor", "kernel": "sandwich_tc_kernel", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(),
             "peak_source": f"{src} bf16_tflops_sustained",
             "flops_per_launch": k_fl / k_n if k_n else None, "avg_launch_ms": k_ms / k_n if k_n else None,
             "launches": k_n}
