@@ -63,7 +63,7 @@ def profiled_traffic():
     except OSError:
         return None
     sha = re.search(r"kernel source sha256: `?([0-9a-f]{64})", text)
-    traffic = re.search(r"traffic per launch: `?([0-9]+) bytes", text)
+    traffic = re.search(r"traffic per launch: `?([0-9]+)`? bytes", text)
     if not sha or not traffic or sha.group(1) != kernel_source_sha():
         return None
     return int(traffic.group(1))
