@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <array>
+#include <map>
 #include <vector>
 
 #include "attn.h"
@@ -88,6 +90,9 @@ struct attn_ctx {
     double flops;
   };
   std::vector<GraphEv>* capture_events = nullptr;
+  // Product split chosen for the tensor-core H_eff, by shape and products per kind
+  // (m0, m1, m2, R0, R1, R2): sweeps rebuild H_eff at every local step.
+  std::map<std::array<int, 6>, int> tc_split_cache;
   void prof_begin(int kid);
   void prof_end(int kid, double flops);
   ~attn_ctx();

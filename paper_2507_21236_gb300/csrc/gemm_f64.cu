@@ -5,9 +5,12 @@
 // (Sec. 4.4.2, Fig. eff-op-cost), the renormalisation T^T (O (x) O) T
 // (Fig. eff-op) and the Gram/projection products of QR. GB300's FP64 rate is
 // low (FMA-bound at about 1.2 TFLOP/s), so the kernel is a plain
-// shared-memory-tiled register-blocked GEMM: 64x64 output tile per 256-thread
-// CTA, 4x4 accumulators per thread, K tile 16; loads pick the coalesced
-// mapping from the unit stride of each operand.
+// shared-memory-tiled register-blocked GEMM: a BM x BN output tile per
+// 256-thread CTA (16 x 16 threads, BM/16 x BN/16 accumulators each), K tile 16;
+// loads pick the coalesced mapping from the unit stride of each operand. The
+// tile is 32 or 64 wide in each direction, chosen from M and N: the mode
+// products of link dimension 32 are batches of 32 x 32 GEMMs, which a 64 x 64
+// tile would compute at a quarter of its width.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,9 +21,11 @@ namespace attn {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
+template <int BM, int BN>
 __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g) {
+  constexpr int TM = BM / 16, TN = BN / 16;  // accumulators per thread
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x;
@@ -34,11 +39,11 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g) {
     const double* Ab = g.A + bh * g.aBhi + bl * g.aBlo;
     const double* Bb = g.B + bh * g.bBhi + bl * g.bBlo;
     double* Cb = g.C + bh * g.cBhi + bl * g.cBlo;
-    double acc[4][4];
+    double acc[TM][TN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
     for (int gg = 0; gg < g.G; ++gg) {
       const double* Ag = Ab + gg * g.aG;
       const double* Bg = Bb + gg * g.bG;
@@ -62,25 +67,25 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g) {
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < BK; ++k) {
-          double a[4], b[4];
+          double a[TM], b[TN];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+          for (int i = 0; i < TM; ++i) a[i] = As[k][ty + 16 * i];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+          for (int j = 0; j < TN; ++j) b[j] = Bs[k][tx + 16 * j];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < TM; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
       }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TM; ++i) {
       int gi = m0 + ty + 16 * i;
       if (gi >= g.M) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < TN; ++j) {
         int gj = n0 + tx + 16 * j;
         if (gj >= g.N) continue;
         double* c = Cb + gi * g.cM + gj * g.cN;
@@ -157,23 +162,31 @@ inline int grid_for(size_t n, int threads = 256, int cap = 4096) {
 
 }  // namespace
 
+// Launch with the tile shape that wastes least of M and N (grid.y > 65535 is rejected).
+cudaError_t launch_gemm(cudaStream_t stream, const GemmF64& g) {
+  const bool sm = g.M <= 32, sn = g.N <= 32;
+  const int bm = sm ? 32 : 64, bn = sn ? 32 : 64;
+  dim3 grid((g.N + bn - 1) / bn, (g.M + bm - 1) / bm, (unsigned)std::min<long>((long)g.Bhi * g.Blo, 65535));
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  if (sm && sn) gemm_f64_kernel<32, 32><<<grid, NT, 0, stream>>>(g);
+  else if (sm) gemm_f64_kernel<32, 64><<<grid, NT, 0, stream>>>(g);
+  else if (sn) gemm_f64_kernel<64, 32><<<grid, NT, 0, stream>>>(g);
+  else gemm_f64_kernel<64, 64><<<grid, NT, 0, stream>>>(g);
+  return cudaGetLastError();
+}
+
 void gemm_f64(attn_ctx* ctx, const GemmF64& g) {
   if (g.M <= 0 || g.N <= 0 || g.Bhi <= 0 || g.Blo <= 0) return;
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, (unsigned)std::min<long>((long)g.Bhi * g.Blo, 65535));
-  ATTN_REQUIRE(grid.y <= 65535, ATTN_EUNSUPPORTED, "GEMM M too large");
+  ATTN_REQUIRE((g.M + 31) / 32 <= 65535, ATTN_EUNSUPPORTED, "GEMM M too large");
   ctx->prof_begin(1);
-  gemm_f64_kernel<<<grid, NT, 0, ctx->stream>>>(g);
+  ATTN_CHECK_CUDA(launch_gemm(ctx->stream, g));
   ctx->prof_end(1, 2.0 * g.M * g.N * (double)g.K * g.G * g.Bhi * g.Blo);
   ctx->launches++;
-  ATTN_CHECK_CUDA(cudaGetLastError());
 }
 
 cudaError_t gemm_f64_stream(cudaStream_t stream, const GemmF64& g) {
   if (g.M <= 0 || g.N <= 0 || g.Bhi <= 0 || g.Blo <= 0) return cudaSuccess;
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, (unsigned)std::min<long>((long)g.Bhi * g.Blo, 65535));
-  if (grid.y > 65535) return cudaErrorInvalidValue;
-  gemm_f64_kernel<<<grid, NT, 0, stream>>>(g);
-  return cudaGetLastError();
+  return launch_gemm(stream, g);
 }
 
 cudaError_t fill_f64_stream(cudaStream_t stream, double* p, size_t n, double v) {

@@ -563,9 +563,30 @@ void attn_heff::apply_bf16(const double* x, double* y) {
     for (int k = 0; k < 3; ++k)
       if (t->R[k]) ATTN_CHECK_CUDA(cudaMemsetAsync(t->y[k].p, 0, sizeof(float) * (size_t)V, st));
   };
+  const std::array<int, 6> key = {m[0], m[1], m[2], t->R[0], t->R[1], t->R[2]};
+  if (t->grid > 0 && !t->tuned) {
+    auto hit = ctx->tc_split_cache.find(key);
+    double fl_all = 0.0;
+    for (int k = 0; k < 3; ++k) fl_all += (double)t->R[k] * 2.0 * (m[kPairP[k]] + m[kPairQ[k]]) * V;
+    if (hit != ctx->tc_split_cache.end()) {
+      t->set_split(hit->second);
+      t->tuned = true;
+    } else if (fl_all < 4e10) {
+      // small operator: no timing, the smallest split that gives every SM a CTA
+      int f = 1;
+      for (int c : {1, 2, 3, 4, 6, 8}) {
+        t->set_split(c);
+        f = c;
+        if (t->grid >= ctx->num_sms) break;
+      }
+      t->set_split(f);
+      t->tuned = true;
+      ctx->tc_split_cache[key] = f;
+    }
+  }
   if (t->grid > 0 && !t->tuned) {
     // Autotuner: time the candidate product splits on this H_eff's real input and
-    // keep the fastest (one-off, at the first BF16 application).
+    // keep the fastest (one-off per shape and product counts, at the first BF16 application).
     cudaEvent_t e0, e1;
     ATTN_CHECK_CUDA(cudaEventCreate(&e0));
     ATTN_CHECK_CUDA(cudaEventCreate(&e1));
@@ -595,6 +616,7 @@ void attn_heff::apply_bf16(const double* x, double* y) {
     cudaEventDestroy(e1);
     t->set_split(best_f);
     t->tuned = true;
+    ctx->tc_split_cache[key] = best_f;
   }
   if (t->grid > 0) {
     // algorithmic FLOPs of this launch: the pair products and the internal operators
