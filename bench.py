@@ -265,14 +265,17 @@ def run_sweeps(args):
     for mode in ("f64", "mixed", "mixed_k3"):
         cfg = attn.attn_config_default()
         if mode == "mixed":
-            # BF16 Lanczos, then FP64 Lanczos from its Ritz vector to the FP64 path's tolerance
+            # BF16 Lanczos, then FP64 Rayleigh-Ritz with BF16 Jacobi-Davidson corrections
+            # to the FP64 path's tolerance
             cfg.matvec_dtype = attn.ATTN_BF16
-            cfg.refine_steps = cfg.lanczos_depth - 1
+            cfg.refine_steps = 8
+            cfg.refine_inner = 16
             cfg.refine_tol = cfg.lanczos_tol
         elif mode == "mixed_k3":
-            # the minimal policy: three FP64 correction steps after the BF16 Lanczos
+            # the minimal policy: three FP64 residual corrections after the BF16 Lanczos
             cfg.matvec_dtype = attn.ATTN_BF16
             cfg.refine_steps = 3
+            cfg.refine_inner = 0
             cfg.refine_tol = 1e-12
         ctx = attn.attn_create(cfg, torch.cuda.current_stream().cuda_stream)
         model = attn.attn_model_tfim(ctx, Ls, h)
@@ -300,8 +303,9 @@ def run_sweeps(args):
             "f64_value": out["f64"]["time_to_1e-8_s"], "final_energy_per_site_diff": d,
             "config": {"workload": f"tfim{Ls}x{Ls}_m{ms}_sweeps", "L": Ls, "m": ms, "h": h,
                        "s_ttn": 1, "lanczos_depth": 20,
-                       "mixed": "bf16 Lanczos + FP64 Lanczos from its Ritz vector to tol 1e-13",
-                       "mixed_k3": "bf16 Lanczos + FP64 Lanczos of depth 4 (three correction steps)"},
+                       "mixed": "bf16 Lanczos + <= 8 FP64 Rayleigh-Ritz corrections from 16-step bf16 CG "
+                                "Jacobi-Davidson solves, to tol 1e-13",
+                       "mixed_k3": "bf16 Lanczos + 3 FP64 residual corrections"},
             "runs": out}
     print(json.dumps(line), flush=True)
 

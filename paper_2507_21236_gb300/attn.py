@@ -30,7 +30,8 @@ class attn_config(ctypes.Structure):
                 ("de_max_iter", ctypes.c_int), ("de_rel_dev", ctypes.c_double),
                 ("s_ttn", ctypes.c_int), ("matvec_dtype", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("refine_tol", ctypes.c_double),
-                ("use_graphs", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("use_graphs", ctypes.c_int), ("refine_inner", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class attn_heff_desc(ctypes.Structure):

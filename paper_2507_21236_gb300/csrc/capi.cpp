@@ -133,6 +133,7 @@ ATTN_API attn_status attn_config_default(attn_config* cfg) {
   cfg->matvec_dtype = ATTN_F64;
   cfg->refine_steps = 3;
   cfg->refine_tol = 1e-10;
+  cfg->refine_inner = 16;
   ATTN_CATCH
 }
 
@@ -628,7 +629,6 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
       const bool prof_was = ctx->prof_on;
       ctx->prof_on = false;
       lanczos_enqueue(ctx, lo, ctx->ws[3].as<double>(), h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0);
-      if (rsteps > 0) lanczos_enqueue(ctx, hi, ctx->ws[3].as<double>(), h->V, rsteps + 1, cfg.refine_tol, g->w, 0);
       ctx->prof_on = prof_was;
       ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
       cudaStream_t user = ctx->stream, cs;
@@ -640,7 +640,6 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
       try {
         ATTN_CHECK_CUDA(ce);
         lanczos_enqueue(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0);
-        if (rsteps > 0) lanczos_enqueue(ctx, hi, T_dev, h->V, rsteps + 1, cfg.refine_tol, g->w, 0);
       } catch (...) {
         cudaGraph_t tmp = nullptr;
         cudaStreamEndCapture(cs, &tmp);
@@ -671,18 +670,27 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
       ctx->prof[e.kid].acc_launches += 1;
     }
     *theta = r.theta;
-    if (iters) *iters = r.iters;
+    int it = r.iters;
+    if (rsteps > 0) {
+      RefineResult f = refine_eig(ctx, hi, lo, T_dev, h->V, rsteps, cfg.refine_inner, cfg.refine_tol, g->rw);
+      *theta = f.theta;
+      it += f.fp64_matvecs + f.lo_matvecs;
+    }
+    if (iters) *iters = it;
     return ATTN_OK;
   }
   LanczosWork w;
   LanczosResult r = lanczos_lowest(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, w);
+  double th = r.theta;
   int it = r.iters;
-  if (dt != ATTN_F64 && cfg.refine_steps > 0) {
-    r = lanczos_lowest(ctx, hi, T_dev, h->V, cfg.refine_steps + 1, cfg.refine_tol, w);
-    it += r.iters;
+  if (rsteps > 0) {
+    RefineWork rw;
+    RefineResult f = refine_eig(ctx, hi, lo, T_dev, h->V, rsteps, cfg.refine_inner, cfg.refine_tol, rw);
+    th = f.theta;
+    it += f.fp64_matvecs + f.lo_matvecs;
   }
   ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
-  *theta = r.theta;
+  *theta = th;
   if (iters) *iters = it;
   ATTN_CATCH
 }

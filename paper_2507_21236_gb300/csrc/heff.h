@@ -15,6 +15,7 @@ struct EigGraph {
   bool prof = false;
   uint64_t launches = 0;
   attn::LanczosWork w;
+  attn::RefineWork rw;
   std::vector<attn_ctx::GraphEv> evs;
   ~EigGraph() {
     if (exec) cudaGraphExecDestroy(exec);

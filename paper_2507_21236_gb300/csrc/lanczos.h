@@ -30,6 +30,26 @@ void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int 
                      int host_check_every);
 LanczosResult lanczos_read(attn_ctx* ctx, LanczosWork& w);
 
+// Mixed-precision refinement of the lowest eigenpair after a low-precision
+// Lanczos: FP64 Rayleigh-Ritz on a subspace grown by corrections from an
+// approximate Jacobi-Davidson solve with `inner` conjugate-gradient steps of the
+// low-precision operator (inner = 0: the residual itself). At most max_outer
+// corrections (one FP64 matvec each); stops when ||H u - theta u|| < tol |theta|.
+// On return x holds the unit Ritz vector u.
+struct RefineResult {
+  double theta;
+  double resid;
+  int outer;         // corrections made
+  int fp64_matvecs;
+  int lo_matvecs;
+  bool converged;
+};
+struct RefineWork {
+  DevBuf Vb, Wb, u, hu, r, t, res, p, q, C;
+};
+RefineResult refine_eig(attn_ctx* ctx, const MatVec& h64, const MatVec& hlo, double* x, long V, int max_outer,
+                        int inner, double tol, RefineWork& w);
+
 // out[i] = <basis_i, w> for i < nvec (deterministic two-pass reduction); accum[i] += out[i] if given.
 void multi_dot(attn_ctx* ctx, const double* basis, int nvec, long V, const double* w, double* out, double* accum);
 void multi_axpy_dev(attn_ctx* ctx, double* w, const double* basis, const double* coef, int nvec, long V, double sign);

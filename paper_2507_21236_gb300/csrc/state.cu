@@ -462,13 +462,15 @@ double attn_state::local_step(int n) {
     ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
     const double e_cur = hv[0] / hv[1];
     LanczosResult r = lanczos_lowest(ctx, mv_lo, v, V, cfg.lanczos_depth, cfg.lanczos_tol, lw);
+    double theta = r.theta;
     if (dt != ATTN_F64 && cfg.refine_steps > 0) {
-      r = lanczos_lowest(ctx, mv64, v, V, cfg.refine_steps + 1, cfg.refine_tol, lw);
+      // FP64 Rayleigh-Ritz with low-precision corrections: theta and v are FP64-exact for this H_eff
+      theta = refine_eig(ctx, mv64, mv_lo, v, V, cfg.refine_steps, cfg.refine_inner, cfg.refine_tol, rfw).theta;
     }
-    if (r.theta <= e_cur + 1e-14 * std::fabs(e_cur)) {
+    if (theta <= e_cur + 1e-14 * std::fabs(e_cur)) {
       std::swap(T[n], tmpT);
       invalidate_from(n);
-      result = r.theta;
+      result = theta;
     } else {
       result = e_cur;
     }

@@ -58,6 +58,7 @@ struct attn_state {
   int learned_used = 0, learned_fallback = 0;
   attn::QRWork qrw;
   attn::LanczosWork lw, lw2;
+  attn::RefineWork rfw;
   attn::DevBuf colbuf, rbuf, tmpT, idxbuf, opsA, opsB, rw1, rw2;
 
   int dim(int n, int s) const { return tree.shape[3 * n + s]; }

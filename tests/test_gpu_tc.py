@@ -160,3 +160,65 @@ def test_mixed_precision_eigsolve_is_fp64_accurate():
     attn.attn_state_destroy(st)
     attn.attn_model_destroy(model)
     attn.attn_destroy(ctx)
+
+
+@pytest.mark.gpu
+def test_mixed_precision_refinement_reaches_fp64_eigenpair():
+    """Jacobi-Davidson refinement with BF16 inner solves (refine_inner > 0) reaches the
+    converged FP64 eigenpair of a physical H_eff (8x8 TFIM, m = 32, top node) within a
+    few FP64 matvecs, while the same number of plain residual corrections (refine_inner
+    = 0) does not; the returned value is the FP64 Rayleigh quotient of the returned
+    vector in both cases (the mixed-precision policy of the local eigenproblem,
+    Sec. 4.4.2)."""
+    from inputs import raw_tree_tensors
+    from oracle.tree import Tree
+    import torch
+
+    attn, ctx = lib_and_ctx()
+    tree = Tree(64, 32)
+    model = attn.attn_model_tfim(ctx, 8, 3.04)
+    st = attn.attn_state_create(ctx, model, 32, raw_tree_tensors(tree.shape, 0))
+    attn.attn_de_place(st, 16)
+    attn.attn_map_hamiltonian(st)
+    attn.attn_ttn_sweep(st)
+    node = tree.top_nodes()[0]
+    attn.attn_move_centre(st, node)
+    H = attn.attn_heff_build(st, node)
+    x0 = attn.attn_node_get(st, node)
+    cfg = attn.attn_get_config(ctx)
+    cfg.lanczos_depth = 60
+    cfg.lanczos_tol = 1e-14
+    cfg.matvec_dtype = attn.ATTN_F64
+    attn.attn_set_config(ctx, cfg)
+    th64, _ = attn.attn_eigsolve(H, dev(x0))
+
+    def rq_and_res(vd):
+        w = torch.empty_like(vd)
+        attn.attn_heff_apply(H, vd, w, attn.ATTN_F64)
+        th = float(torch.dot(vd.reshape(-1), w.reshape(-1)) / torch.dot(vd.reshape(-1), vd.reshape(-1)))
+        return th, float(torch.linalg.norm(w - th * vd))
+
+    out = {}
+    for inner in (0, 16):
+        cfg.lanczos_depth = 20
+        cfg.lanczos_tol = 1e-13
+        cfg.matvec_dtype = attn.ATTN_BF16
+        cfg.refine_steps = 5
+        cfg.refine_tol = 1e-13
+        cfg.refine_inner = inner
+        attn.attn_set_config(ctx, cfg)
+        t = dev(x0)
+        th, _ = attn.attn_eigsolve(H, t)
+        rq, res = rq_and_res(t)
+        assert abs(th - rq) < 1e-12 * abs(rq)
+        assert th >= th64 - 1e-11 * abs(th64)
+        out[inner] = (th - th64, res)
+    # five corrections with BF16 inner solves: FP64-level eigenvalue and eigenvector
+    assert out[16][0] < 1e-11 * abs(th64), out
+    assert out[16][1] < 1e-6 * abs(th64), out
+    # five plain residual corrections leave a clearly larger error
+    assert out[0][0] > 10 * out[16][0] and out[0][1] > 10 * out[16][1], out
+    attn.attn_heff_destroy(H)
+    attn.attn_state_destroy(st)
+    attn.attn_model_destroy(model)
+    attn.attn_destroy(ctx)
