@@ -163,7 +163,9 @@ ATTN_API attn_status attn_node_neighbour(attn_state* st, int node, int slot, int
  * the effective operators that depend on it. */
 ATTN_API attn_status attn_node_get(attn_state* st, int node, double* host_out);
 ATTN_API attn_status attn_node_set(attn_state* st, int node, const double* host_in);
-/* Device pointer of a node tensor (valid until the node changes shape/state is destroyed). */
+/* Device pointer of a node tensor, for reading (valid until the state is destroyed or
+ * the centre moves through the node). Change a tensor with attn_node_set, which
+ * invalidates the effective operators and the cached state energy that depend on it. */
 ATTN_API attn_status attn_node_device_ptr(attn_state* st, int node, double** dev_ptr);
 /* Move the isometry centre along the tree path with one QR per link (Fig. iso). */
 ATTN_API attn_status attn_move_centre(attn_state* st, int node);

@@ -376,6 +376,7 @@ ATTN_API attn_status attn_node_set(attn_state* st, int node, const double* host_
                                   st->ctx->stream));
   ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
   st->invalidate_from(node);
+  st->energy_known = std::nan("");
   ATTN_CATCH
 }
 

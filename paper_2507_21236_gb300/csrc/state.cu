@@ -113,6 +113,7 @@ void attn_state::init_from_raw(const double* const* raw) {
   for (int n = 0; n < N; ++n)
     for (int s = 0; s < 3; ++s) env[3 * n + s].dim = dim(n, s);
   mapped_ready = false;
+  energy_known = std::nan("");
 }
 
 void attn_state::invalidate_from(int c) {
@@ -162,6 +163,7 @@ void attn_state::set_products() {
   prods = split_products(mapped);
   for (auto& e : env) e.valid = false;
   mapped_ready = true;
+  energy_known = std::nan("");
 }
 
 // ------------------------------------------------------- link operators
@@ -450,29 +452,36 @@ double attn_state::local_step(int n) {
       if (dt == ATTN_BF16) h->apply_bf16(a, b); else h->apply_f64(a, b);
     };
     MatVec mv64 = [&](const double* a, double* b) { h->apply_f64(a, b); };
-    // current energy (FP64)
-    lw2.wvec.reserve(sizeof(double) * V);
-    ctx->scal.reserve(sizeof(double) * 64);
-    double* s = ctx->scal.as<double>();
-    h->apply_f64(tensor(n), lw2.wvec.as<double>());
-    multi_dot(ctx, tensor(n), 1, V, lw2.wvec.as<double>(), s, nullptr);
-    multi_dot(ctx, tensor(n), 1, V, tensor(n), s + 1, nullptr);
-    double hv[2];
-    ATTN_CHECK_CUDA(cudaMemcpyAsync(hv, s, sizeof(hv), cudaMemcpyDeviceToHost, ctx->stream));
-    ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
-    const double e_cur = hv[0] / hv[1];
+    // current energy (FP64): known from the last local step unless H' or a tensor changed since
+    double e_cur = energy_known;
+    if (!std::isfinite(e_cur)) {
+      lw2.wvec.reserve(sizeof(double) * V);
+      ctx->scal.reserve(sizeof(double) * 64);
+      double* s = ctx->scal.as<double>();
+      h->apply_f64(tensor(n), lw2.wvec.as<double>());
+      multi_dot(ctx, tensor(n), 1, V, lw2.wvec.as<double>(), s, nullptr);
+      multi_dot(ctx, tensor(n), 1, V, tensor(n), s + 1, nullptr);
+      double hv[2];
+      ATTN_CHECK_CUDA(cudaMemcpyAsync(hv, s, sizeof(hv), cudaMemcpyDeviceToHost, ctx->stream));
+      ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+      e_cur = hv[0] / hv[1];
+    }
     LanczosResult r = lanczos_lowest(ctx, mv_lo, v, V, cfg.lanczos_depth, cfg.lanczos_tol, lw);
     double theta = r.theta;
+    bool exact = (dt == ATTN_F64);
     if (dt != ATTN_F64 && cfg.refine_steps > 0) {
       // FP64 Rayleigh-Ritz with low-precision corrections: theta and v are FP64-exact for this H_eff
       theta = refine_eig(ctx, mv64, mv_lo, v, V, cfg.refine_steps, cfg.refine_inner, cfg.refine_tol, rfw).theta;
+      exact = true;
     }
     if (theta <= e_cur + 1e-14 * std::fabs(e_cur)) {
       std::swap(T[n], tmpT);
       invalidate_from(n);
       result = theta;
+      energy_known = exact ? theta : std::nan("");
     } else {
       result = e_cur;
+      energy_known = e_cur;
     }
   } catch (...) {
     delete h;

@@ -1,6 +1,8 @@
 // TTN state with per-link effective operators (internal).
 #pragma once
 
+#include <cmath>
+
 #include <utility>
 #include <vector>
 
@@ -50,6 +52,10 @@ struct attn_state {
   std::vector<attn::Prod> prods;
   std::vector<attn::Env> env;  // [node*3 + slot]
   bool mapped_ready = false;
+  // FP64 energy <psi|H'|psi> of the current state when known exactly (after a local
+  // step with an FP64-exact Ritz value; centre moves are gauge changes and keep it),
+  // NaN otherwise. Saves the FP64 matvec that prices the current tensor.
+  double energy_known = std::nan("");
   int sweep_count = 0;
   std::vector<double> last_de_energy;  // [k][2]: E_k before / after the last update
   bool first_de_done = false;          // the first disentangler update of this state ran
