@@ -266,17 +266,17 @@ def run_sweeps(args):
         cfg = attn.attn_config_default()
         if mode == "mixed":
             # BF16 Lanczos, then FP64 Rayleigh-Ritz with BF16 Jacobi-Davidson corrections
-            # to the FP64 path's tolerance
+            # until theta moves by < 1e-10 |theta| (more accurate per local step than
+            # the FP64 path's depth-20 Lanczos)
             cfg.matvec_dtype = attn.ATTN_BF16
             cfg.refine_steps = 8
             cfg.refine_inner = 16
-            cfg.refine_tol = cfg.lanczos_tol
+            cfg.refine_tol = 1e-10
         elif mode == "mixed_k3":
-            # the minimal policy: three FP64 residual corrections after the BF16 Lanczos
+            # the library default: three such corrections
             cfg.matvec_dtype = attn.ATTN_BF16
             cfg.refine_steps = 3
-            cfg.refine_inner = 0
-            cfg.refine_tol = 1e-12
+            cfg.refine_inner = 16
         ctx = attn.attn_create(cfg, torch.cuda.current_stream().cuda_stream)
         model = attn.attn_model_tfim(ctx, Ls, h)
         st = attn.attn_state_create(ctx, model, ms, raw)
@@ -304,8 +304,8 @@ def run_sweeps(args):
             "config": {"workload": f"tfim{Ls}x{Ls}_m{ms}_sweeps", "L": Ls, "m": ms, "h": h,
                        "s_ttn": 1, "lanczos_depth": 20,
                        "mixed": "bf16 Lanczos + <= 8 FP64 Rayleigh-Ritz corrections from 16-step bf16 CG "
-                                "Jacobi-Davidson solves, to tol 1e-13",
-                       "mixed_k3": "bf16 Lanczos + 3 FP64 residual corrections"},
+                                "Jacobi-Davidson solves, until theta moves by < 1e-10 |theta|",
+                       "mixed_k3": "bf16 Lanczos + 3 such corrections (library default)"},
             "runs": out}
     print(json.dumps(line), flush=True)
 

@@ -82,7 +82,8 @@ typedef struct {
   int s_ttn;                /* sweeps without disentangler optimisation, Sec. 6.3 (1) */
   attn_dtype matvec_dtype;  /* precision of the H_eff contractions in Lanczos (ATTN_F64) */
   int refine_steps;         /* FP64 corrections (one FP64 matvec each) after a low-precision Lanczos (3) */
-  double refine_tol;        /* stop refining when ||H v - theta v|| < tol |theta| (1e-10) */
+  double refine_tol;        /* stop refining when ||H v - theta v|| < tol |theta| or a correction
+                               lowers theta by at most tol |theta| (1e-10) */
   int use_graphs;           /* attn_eigsolve replays a captured CUDA graph of the low-precision Lanczos (0) */
   int refine_inner;         /* conjugate-gradient steps of the low-precision H_eff per correction, solving the
                                Jacobi-Davidson correction equation; 0 = the residual itself (16) */

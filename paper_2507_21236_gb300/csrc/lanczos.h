@@ -34,7 +34,8 @@ LanczosResult lanczos_read(attn_ctx* ctx, LanczosWork& w);
 // Lanczos: FP64 Rayleigh-Ritz on a subspace grown by corrections from an
 // approximate Jacobi-Davidson solve with `inner` conjugate-gradient steps of the
 // low-precision operator (inner = 0: the residual itself). At most max_outer
-// corrections (one FP64 matvec each); stops when ||H u - theta u|| < tol |theta|.
+// corrections (one FP64 matvec each); stops when ||H u - theta u|| < tol |theta|
+// or when the last correction lowered theta by at most tol |theta|.
 // On return x holds the unit Ritz vector u.
 struct RefineResult {
   double theta;
