@@ -21,6 +21,7 @@ bounded sample (a subset of the node's products), scaled to matvecs/s.
 import argparse
 import hashlib
 import json
+import math
 import re
 import os
 import statistics
@@ -310,9 +311,122 @@ def run_sweeps(args):
     print(json.dumps(line), flush=True)
 
 
+# (name, model, L, m, coupling): the matvec benchmark shapes of every configuration
+NODE_CONFIGS = [("C2", "tfim", 8, 32, 3.04), ("C3", "tfim", 16, 64, 3.04), ("C3", "tfim", 16, 128, 3.04),
+                ("C4", "heis", 16, 64, 1.0), ("C4", "heis", 16, 128, 1.0), ("C5", "tfim", 32, 128, 3.04)]
+
+
+def tree_shapes(n, m):
+    """[child, child, parent] shapes of the binary tree over n sites, layer by layer."""
+    nL = n.bit_length() - 2
+    cap = lambda e: m if e >= 5 else min(2 ** (2 ** e), m)
+    shapes = []
+    for l in range(1, nL + 1):
+        cd = 2 if l == 1 else cap(l - 1)
+        pd = cap(l) if l < nL else cap(nL)
+        shapes += [(cd, cd, pd)] * (n >> l)
+    return shapes
+
+
+def config_counts(attn, ctx, model_kind, Ls, coupling):
+    """Per-node product counts of a configuration after mapping through seeded
+    random orthogonal disentanglers (the bookkeeping is the same for every m in
+    [16, 255], so it is queried on an m = 16 tree)."""
+    from inputs import normal, raw_tree_tensors
+
+    n = Ls * Ls
+    model = (attn.attn_model_tfim(ctx, Ls, coupling) if model_kind == "tfim"
+             else attn.attn_model_tri_heisenberg(ctx, Ls, coupling))
+    st = attn.attn_state_create(ctx, model, 16, raw_tree_tensors(tree_shapes(n, 16), 0))
+    n_de = attn.attn_de_place(st, n // 4)
+    for k in range(n_de):
+        q, r = np.linalg.qr(normal(11, 5000 + k, 16).reshape(4, 4))
+        attn.attn_de_set(st, k, q * np.sign(np.diag(r)))
+    attn.attn_map_hamiltonian(st)
+    nn = attn.attn_state_info(st)[0]
+    counts = [attn.attn_heff_counts(st, i) for i in range(nn)]
+    attn.attn_state_destroy(st)
+    attn.attn_model_destroy(model)
+    return n_de, counts
+
+
+def run_nodes(args):
+    """H_eff apply time of every [m,m,m] node of each configuration, BF16 tensor-core
+    path (all nodes) and FP64 path (a sample), with the nodes' real product counts."""
+    import torch
+    from __graft_entry__ import build
+    from paper_2507_21236_gb300 import attn
+
+    build()
+    torch.cuda.set_device(0)
+    ctx = attn.attn_create(attn.attn_config_default(), torch.cuda.current_stream().cuda_stream)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    stream = torch.cuda.current_stream()
+    out = []
+
+    def timed_apply(H, x, y, dt, reps):
+        attn.attn_heff_apply(H, x.data_ptr(), y.data_ptr(), dt)  # warm-up (first BF16 call builds and tunes)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            attn.attn_heff_apply(H, x.data_ptr(), y.data_ptr(), dt)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    for name, kind, Ls, m, coupling in NODE_CONFIGS:
+        n_de, counts = config_counts(attn, ctx, kind, Ls, coupling)
+        shapes = tree_shapes(Ls * Ls, m)
+        big = [i for i, sh in enumerate(shapes) if sh == (m, m, m)]
+        rmax = max(max(counts[i][:4]) for i in big)
+        pool = torch.randn((2, rmax, m, m), device="cuda", dtype=torch.float64, generator=gen) / math.sqrt(m)
+        hint = [torch.randn((m, m), device="cuda", dtype=torch.float64, generator=gen) / math.sqrt(m) for _ in range(3)]
+        x = torch.randn((m, m, m), device="cuda", dtype=torch.float64, generator=gen)
+        y = torch.empty_like(x)
+        rows, by_counts = [], {}
+        for i in big:
+            c = counts[i]
+            key = tuple(c[:4])
+            if key not in by_counts:
+                pairs = {k: (pool[0, :c[k]], pool[1, :c[k]]) for k in range(3) if c[k]}
+                trip = tuple(pool[s % 2, :c[3]] for s in range(3)) if c[3] else None
+                H = attn.attn_heff_create(ctx, (m, m, m), hint, pairs, trip)
+                fl = attn.attn_heff_info(H)[2]
+                ms = timed_apply(H, x, y, attn.ATTN_BF16, 5)
+                by_counts[key] = (fl, ms, H)
+            fl, ms, _ = by_counts[key]
+            rows.append({"node": i, "counts": list(c[:4]), "gflop": fl / 1e9, "bf16_ms": ms})
+        # FP64 on a sample: the lightest, the median and the heaviest node
+        srt = sorted(rows, key=lambda r: r["gflop"])
+        sample = [srt[0], srt[len(srt) // 2], srt[-1]]
+        for r in sample:
+            H = by_counts[tuple(r["counts"])][2]
+            r["f64_ms"] = timed_apply(H, x, y, attn.ATTN_F64, 1)
+        for _, _, H in by_counts.values():
+            attn.attn_heff_destroy(H)
+        del pool
+        tot_fl = sum(r["gflop"] for r in rows)
+        tot_bf = sum(r["bf16_ms"] for r in rows)
+        f64_fl = sum(r["gflop"] for r in sample)
+        f64_ms = sum(r["f64_ms"] for r in sample)
+        out.append({"config": name, "model": kind, "L": Ls, "m": m, "n_de_placed": n_de, "nodes": len(rows),
+                    "products_per_node": [min(sum(r["counts"]) for r in rows), max(sum(r["counts"]) for r in rows)],
+                    "gflop_per_matvec": [round(srt[0]["gflop"], 2), round(srt[-1]["gflop"], 2)],
+                    "bf16": {"ms_all_nodes": round(tot_bf, 3), "tflops_flop_weighted": tot_fl / tot_bf,
+                             "tflops_top": rows[-1]["gflop"] / rows[-1]["bf16_ms"]},
+                    "f64_sample": {"nodes": [r["node"] for r in sample],
+                                   "ms": [round(r["f64_ms"], 3) for r in sample],
+                                   "tflops_flop_weighted": f64_fl / f64_ms},
+                    "bf16_speedup_on_sample": f64_ms / sum(r["bf16_ms"] for r in sample)})
+        print(json.dumps(out[-1]), flush=True)
+    print(json.dumps({"metric": "H_eff apply per [m,m,m] node, BF16 tensor cores vs FP64",
+                      "unit": "TFLOP/s", "configs": out}), flush=True)
+    attn.attn_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="matvec", choices=["matvec", "sweep"])
+    ap.add_argument("--mode", default="matvec", choices=["matvec", "sweep", "nodes"])
     ap.add_argument("--sweep-L", type=int, default=16)
     ap.add_argument("--sweep-m", type=int, default=32)
     ap.add_argument("--max-sweeps", type=int, default=30)
@@ -326,6 +440,8 @@ def main():
         return run_reference(args)
     if args.mode == "sweep":
         return run_sweeps(args)
+    if args.mode == "nodes":
+        return run_nodes(args)
     args.warmup = max(args.warmup, 3)
 
     import torch
