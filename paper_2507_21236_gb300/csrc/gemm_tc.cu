@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(kTnThreads, 2) tn_gemm_kernel(const __grid_con
     const int q4 = warp & 3;
     const int i = m0 + q4 * 32 + lane;
     const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
-    if (nk > 0 && mbar_wait(bar(DONE), 0, p.err, 53, abort_flag)) {
+    // warp-uniform: the TMEM loads below are .sync.aligned
+    if (nk > 0 && __all_sync(0xffffffffu, mbar_wait(bar(DONE), 0, p.err, 53, abort_flag))) {
       fence_after();
       const long cbase = (long)bhi * p.c_bhi + (long)blo * p.c_blo + (long)i * p.c_rs;
       for (int c0 = 0; c0 < 128; c0 += 32) {

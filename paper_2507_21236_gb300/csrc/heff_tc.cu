@@ -30,14 +30,21 @@
 // and stage-1 MMA issue, warp 2 = stage-2 MMA issue, warps 4-19 = conversion
 // and epilogue, eight per slice in two
 // column halves (warp w reads TMEM lanes 32*(w%4) .. +31). Internal
-// (single-link) operators enter as products with an identity partner;
-// three-link products go through the FP64 path. Every mbarrier wait is
+// (single-link) operators enter as products with an identity partner.
+//
+// A three-link product A_r (x) B_r (x) C_r (slots 0, 1, 2) is applied in two
+// steps: a batched TN GEMM contracts slot 2 with C_r, giving per product the
+// slice stack W_r[c] = (x x_2 C_r)[:, :, c] in the layout of the pair kind (0, 1);
+// the same kernel then runs in per-product mode (kPP), where each product brings
+// its own X slices through the ring (B_r, X_{r,s0}, X_{r,s0+1}, A_r) and the
+// result adds onto the kind-(0, 1) output. Every mbarrier wait is
 // bounded (about 2 s of clock); on timeout the kernel records an error code,
 // stops issuing work, waits (bounded) for its in-flight copies, frees TMEM and
 // returns.
 #include <algorithm>
 #include <cstring>
 
+#include "gemm_tc.h"
 #include "heff.h"
 #include "tc_ptx.h"
 
@@ -67,6 +74,7 @@ constexpr int kHalfWarps = 4;         // conversion warps per slice half (one Z-
 constexpr int kTileBytes = 128 * 128 * 2;  // one 128 x 128 BF16 tile (two 64-wide K blocks)
 constexpr int kKBlockBytes = 128 * 128;    // 128 rows x 128 bytes
 constexpr int kStages = 10;                // operator ring depth (K blocks)
+constexpr int kStagesPP = 14;              // ring depth when every product brings its own slices
 constexpr uint32_t kTmemCols = 512;
 
 struct KindParams {
@@ -74,6 +82,7 @@ struct KindParams {
   int rsplit;         // CTAs per slice pair, each owning a contiguous range of products
   int cta_begin;      // first CTA index of this kind
   float* Y;           // [S][P][Q] fp32 output (written, or accumulated when rsplit > 1)
+  int accumulate;     // add to Y instead of writing it
 };
 
 struct TcParams {
@@ -92,26 +101,31 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 // ------------------------------------------------------------------ kernel
+// kPP = false: the CTA's two X slices are loaded once and serve every product.
+// kPP = true: product r has its own slices (slice z = r S + s of the X map),
+// streamed through the ring between B_r and A_r.
+template <bool kPP>
 __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_constant__ TcMaps maps, TcParams prm) {
+  constexpr int NS = kPP ? kStagesPP : kStages;
   extern __shared__ uint8_t smem_raw[];
   // 1024-aligned regions: X of both slices (K block kb of slice u at
-  // 32 KB kb + 16 KB u), operator ring, barriers.
+  // 32 KB kb + 16 KB u; absent when kPP), operator ring, barriers.
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
   const uint32_t sX = base;
-  const uint32_t sRing = base + 2 * kTileBytes;
-  const uint32_t sBar = sRing + kStages * kKBlockBytes;
+  const uint32_t sRing = kPP ? base : base + 2 * kTileBytes;
+  const uint32_t sBar = sRing + NS * kKBlockBytes;
   enum {
     XFULL = 0,
     FULL = 1,
-    EMPTY = 1 + kStages,
-    D1FULL = 1 + 2 * kStages,  // [slice]: stage 1 done
-    ZFULL = 3 + 2 * kStages,   // [slice][half]: that half of Z^T packed in TMEM
-    S2DONE = 7 + 2 * kStages,  // [slice]: stage 2 done, D1 free for the next product
-    D2FULL = 9 + 2 * kStages,
-    S1END = 10 + 2 * kStages,  // every stage-1 MMA complete (TMEM may be freed)
-    NBAR = 11 + 2 * kStages
+    EMPTY = 1 + NS,
+    D1FULL = 1 + 2 * NS,  // [slice]: stage 1 done
+    ZFULL = 3 + 2 * NS,   // [slice][half]: that half of Z^T packed in TMEM
+    S2DONE = 7 + 2 * NS,  // [slice]: stage 2 done, D1 free for the next product
+    D2FULL = 9 + 2 * NS,
+    S1END = 10 + 2 * NS,  // every stage-1 MMA complete (TMEM may be freed)
+    NBAR = 11 + 2 * NS
   };
   uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + (sBar - base));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBAR);
@@ -135,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
 
   if (threadIdx.x == 0) {
     mbar_init(bar(XFULL), 1);
-    for (int i = 0; i < kStages; ++i) {
+    for (int i = 0; i < NS; ++i) {
       mbar_init(bar(FULL + i), 1);
       mbar_init(bar(EMPTY + i), 1);
     }
@@ -168,40 +182,47 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
   const CUtensorMap* mB = &maps.b[kind];
 
   if (warp == 0 && lane == 0) {
-    // ---- producer: X of both slices once, then operator K blocks in consumption order
-    mbar_expect_tx(bar(XFULL), (uint32_t)(nsl * nkbQ * P * 128));
-    for (int u = 0; u < nsl; ++u)
-      for (int kb = 0; kb < nkbQ; ++kb)
-        tma_load_3d(sX + kb * kTileBytes + u * (kTileBytes / 2), mX, 64 * kb, 0, s0 + u, bar(XFULL));
+    // ---- producer: X of both slices once (or per product when kPP), then the
+    // operator K blocks in consumption order
+    if (!kPP) {
+      mbar_expect_tx(bar(XFULL), (uint32_t)(nsl * nkbQ * P * 128));
+      for (int u = 0; u < nsl; ++u)
+        for (int kb = 0; kb < nkbQ; ++kb)
+          tma_load_3d(sX + kb * kTileBytes + u * (kTileBytes / 2), mX, 64 * kb, 0, s0 + u, bar(XFULL));
+    }
     int issued = 0;
     int st = 0;       // ring stage of the next load
     uint32_t ph = 0;  // parity of that stage's current fill
     bool ok = true;
+    const int nparts = kPP ? 2 + nsl : 2;  // B_r, [X_{r,s0}, X_{r,s0+1}], A_r
     for (int r = 0; ok && r < R; ++r) {
-      for (int half = 0; ok && half < 2; ++half) {
-        const CUtensorMap* mp = half == 0 ? mB : mA;
-        const int nkb = half == 0 ? nkbQ : nkbP;
+      for (int part = 0; ok && part < nparts; ++part) {
+        const bool isB = part == 0, isA = part == nparts - 1;
+        const CUtensorMap* mp = isB ? mB : (isA ? mA : mX);
+        const int nkb = isA ? nkbP : nkbQ;
+        const int z = isB || isA ? r_begin + r : (r_begin + r) * kp.S + s0 + (part - 1);
+        const uint32_t bytes = isB || isA ? (uint32_t)kKBlockBytes : (uint32_t)(P * 128);
         for (int kb = 0; kb < nkb; ++kb) {
           // the stage's previous contents (fill ph - 1) must have been consumed
-          if (issued >= kStages && !mbar_wait(bar(EMPTY + st), ph ^ 1u, prm.err, 11, abort_flag)) {
+          if (issued >= NS && !mbar_wait(bar(EMPTY + st), ph ^ 1u, prm.err, 11, abort_flag)) {
             ok = false;
             break;
           }
-          mbar_expect_tx(bar(FULL + st), (uint32_t)kKBlockBytes);
-          tma_load_3d(sRing + st * kKBlockBytes, mp, 64 * kb, 0, r_begin + r, bar(FULL + st));
+          mbar_expect_tx(bar(FULL + st), bytes);
+          tma_load_3d(sRing + st * kKBlockBytes, mp, 64 * kb, 0, z, bar(FULL + st));
           ++issued;
-          if (++st == kStages) { st = 0; ph ^= 1u; }
+          if (++st == NS) { st = 0; ph ^= 1u; }
         }
       }
     }
     // drain: wait (bounded) until every issued load has landed
-    {
+    if (!kPP) {
       long long t0 = clock64();
       while (!mbar_try_wait(bar(XFULL), 0) && clock64() - t0 < kWaitCycles) {}
     }
-    for (int q = (issued > kStages ? issued - kStages : 0); q < issued; ++q) {
+    for (int q = (issued > NS ? issued - NS : 0); q < issued; ++q) {
       long long t0 = clock64();
-      while (!mbar_try_wait(bar(FULL + q % kStages), (q / kStages) & 1) && clock64() - t0 < kWaitCycles) {}
+      while (!mbar_try_wait(bar(FULL + q % NS), (q / NS) & 1) && clock64() - t0 < kWaitCycles) {}
     }
   } else if ((warp == 1 || warp == 2) && lane == 0) {
     // ---- MMA issue, split over two threads on different SM sub-partitions: a
@@ -216,11 +237,12 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     uint32_t ph = 0;   // its phase parity
     auto advance = [&](int n) {
       for (int i = 0; i < n; ++i)
-        if (++st == kStages) { st = 0; ph ^= 1u; }
+        if (++st == NS) { st = 0; ph ^= 1u; }
     };
+    const int nkbX = kPP ? nsl * nkbQ : 0;  // ring K blocks of X per product
     if (warp == 1) {
       const uint64_t dX0 = sw128_desc(sX);  // X block kb of slice u: + (32 KB kb + 16 KB u) >> 4
-      bool ok = mbar_wait(bar(XFULL), 0, prm.err, 31, abort_flag);
+      bool ok = kPP ? true : mbar_wait(bar(XFULL), 0, prm.err, 31, abort_flag);
       for (int r = 0; ok && r < R; ++r) {
         // stage 1 per slice: D1_u = B_r X_u^T (the B_r blocks serve both slices)
         for (int u = 0; ok && u < nsl; ++u) {
@@ -229,10 +251,15 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
           fence_after();
           int s1 = st;
           uint32_t p1 = ph;
+          int sx = st + nkbQ * (1 + u);  // ring stage of this slice's first X block (kPP)
+          uint32_t px = ph;
+          while (sx >= NS) { sx -= NS; px ^= 1u; }
           for (int kb = 0; kb < nkbQ; ++kb) {
             if (u == 0 && !mbar_wait(barFull + 8 * s1, p1, prm.err, 32, abort_flag)) { ok = false; break; }
+            if (kPP && !mbar_wait(barFull + 8 * sx, px, prm.err, 36, abort_flag)) { ok = false; break; }
             const uint64_t dB = dRing0 + (uint64_t)(s1 * (kKBlockBytes >> 4));
-            const uint64_t dX = dX0 + (uint64_t)((kb * kTileBytes + u * (kTileBytes / 2)) >> 4);
+            const uint64_t dX = kPP ? dRing0 + (uint64_t)(sx * (kKBlockBytes >> 4))
+                                    : dX0 + (uint64_t)((kb * kTileBytes + u * (kTileBytes / 2)) >> 4);
             const int n4 = nk16Q - 4 * kb;
             if (n4 >= 4) {
               mma4_ss(tD1(u), dB, dX, id, kb > 0 ? 1u : 0u);
@@ -241,12 +268,14 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
                 mma_bf16(tD1(u), dB + 2 * k4, dX + 2 * k4, id, (kb > 0 || k4 > 0) ? 1u : 0u);
             }
             if (u == nsl - 1) mma_commit(barEmpty + 8 * s1);
-            if (++s1 == kStages) { s1 = 0; p1 ^= 1u; }
+            if (kPP) mma_commit(barEmpty + 8 * sx);
+            if (++s1 == NS) { s1 = 0; p1 ^= 1u; }
+            if (++sx == NS) { sx = 0; px ^= 1u; }
           }
           if (!ok) break;
           mma_commit(bar(D1FULL + u));
         }
-        advance(nkbQ + nkbP);
+        advance(nkbQ + nkbX + nkbP);
       }
       mma_commit(bar(S1END));
       long long t0 = clock64();
@@ -254,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     } else {
       bool ok = true;
       for (int r = 0; ok && r < R; ++r) {
-        advance(nkbQ);
+        advance(nkbQ + nkbX);
         // stage 2 per slice: D2_u += Z_u^T A_r^T, Z_u read from TMEM half by half
         for (int u = 0; ok && u < nsl; ++u) {
           int s2 = st;
@@ -273,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
                 mma_bf16_ts(tD2(u), aZ + 8 * k4, dA + 2 * k4, id, (r > 0 || kb > 0 || k4 > 0) ? 1u : 0u);
             }
             if (u == nsl - 1) mma_commit(barEmpty + 8 * s2);
-            if (++s2 == kStages) { s2 = 0; p2 ^= 1u; }
+            if (++s2 == NS) { s2 = 0; p2 ^= 1u; }
           }
           if (!ok) break;
           mma_commit(bar(S2DONE + u));
@@ -318,7 +347,8 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     if (ok && R > 0 && __all_sync(0xffffffffu, mbar_wait(bar(D2FULL), 0, prm.err, 43, abort_flag))) {
       fence_after();
       float* yp = kp.Y + ((long)(s0 + u) * P + c0) * Q + j;  // walks down column j of Y_s
-      const bool add = kp.rsplit > 1;  // partial sums of a split product list meet here
+      // partial sums of a split product list meet here, and per-product results add onto the pair result
+      const bool add = kp.rsplit > 1 || kp.accumulate;
       for (int cc = c0; cc < c0 + 64 && cc < P; cc += 32) {
         float v[32];
         tmem_ld32(tD2(u) + lane_off + cc, v);  // v[c] = Y_s[cc + c][j]
@@ -436,6 +466,12 @@ struct TcState {
   size_t smem = 0;
   int rsplit = 1;        // products of a slice split over this many CTAs (autotuned)
   bool tuned = false;
+  // three-link products: bf16 factors per slot, the slot-2 contraction of one chunk
+  // of products ([tchunk][m2][m0][m1]) and the per-product kernel's maps and parameters
+  int nt = 0, tchunk = 0;
+  DevBuf t0, t1, t2, w;
+  TcMaps tmaps;
+  TcParams tprm;
   // Split every kind's product list f ways (at least 8 products per CTA) and lay out
   // the grid: one CTA per slice pair and product range.
   void set_split(int f) {
@@ -519,6 +555,7 @@ static void tc_build(attn_heff* h) {
     KindParams& kp = t->prm.kind[nk];
     kp.P = P; kp.Q = Q; kp.S = S; kp.R = R; kp.cta_begin = cta; kp.Y = t->y[k].as<float>();
     kp.rsplit = 1;
+    kp.accumulate = 0;
     cta += (S + 1) / 2;
     ++nk;
   }
@@ -527,8 +564,38 @@ static void tc_build(attn_heff* h) {
   t->err.reserve(sizeof(int));
   ATTN_CHECK_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), st));
   t->prm.err = t->err.as<int>();
-  t->smem = 1024 + 2 * (size_t)kTileBytes + (size_t)kStages * kKBlockBytes + 256;
-  ATTN_CHECK_CUDA(cudaFuncSetAttribute(sandwich_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem));
+  if (h->ntrip > 0) {
+    // three-link products: W_r = x x_2 C_r lands in the kind-(0, 1) slice layout
+    // [c][a][b] and the per-product kernel adds A_r W_r[c] B_r^T onto Y01
+    const int nt = h->ntrip, P = m[0], Q = m[1], S = m[2];
+    t->nt = nt;
+    t->t0.reserve(sizeof(__nv_bfloat16) * (size_t)nt * P * P);
+    t->t1.reserve(sizeof(__nv_bfloat16) * (size_t)nt * Q * Q);
+    t->t2.reserve(sizeof(__nv_bfloat16) * (size_t)nt * S * S);
+    to_bf16_kernel<<<vgrid((long)nt * P * P), 256, 0, st>>>(t->t0.as<__nv_bfloat16>(), h->tr[0].as<double>(), (long)nt * P * P);
+    to_bf16_kernel<<<vgrid((long)nt * Q * Q), 256, 0, st>>>(t->t1.as<__nv_bfloat16>(), h->tr[1].as<double>(), (long)nt * Q * Q);
+    to_bf16_kernel<<<vgrid((long)nt * S * S), 256, 0, st>>>(t->t2.as<__nv_bfloat16>(), h->tr[2].as<double>(), (long)nt * S * S);
+    ctx->launches += 3;
+    // products per chunk: W of one chunk stays under 1 GiB
+    t->tchunk = (int)std::min<long>(nt, std::max<long>(8, (1L << 29) / std::max<long>(h->V, 1)));
+    t->w.reserve(sizeof(__nv_bfloat16) * (size_t)t->tchunk * h->V);
+    if (!t->R[0]) t->y[0].reserve(sizeof(float) * (size_t)h->V);
+    if (!t->R[2]) t->x[2].reserve(sizeof(__nv_bfloat16) * (size_t)h->V);
+    encode_map(&t->tmaps.x[0], t->w.p, Q, P, t->tchunk * S, P);
+    encode_map(&t->tmaps.a[0], t->t0.p, P, P, nt, 128);
+    encode_map(&t->tmaps.b[0], t->t1.p, Q, Q, nt, 128);
+    KindParams& kp = t->tprm.kind[0];
+    kp.P = P; kp.Q = Q; kp.S = S; kp.R = 0; kp.rsplit = 1; kp.cta_begin = 0;
+    kp.Y = t->y[0].as<float>();
+    kp.accumulate = 1;
+    t->tprm.nkinds = 1;
+    t->tprm.err = t->err.as<int>();
+  }
+  t->smem = 1024 + 2 * (size_t)kTileBytes + (size_t)kStages * kKBlockBytes + 512;
+  static_assert(2 * kTileBytes + kStages * kKBlockBytes == kStagesPP * kKBlockBytes,
+                "both kernel modes use the same shared-memory size");
+  ATTN_CHECK_CUDA(cudaFuncSetAttribute(sandwich_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem));
+  ATTN_CHECK_CUDA(cudaFuncSetAttribute(sandwich_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem));
   ATTN_CHECK_CUDA(cudaGetLastError());
   h->tc_ready = true;
 }
@@ -557,7 +624,7 @@ void attn_heff::apply_bf16(const double* x, double* y) {
   // the kind buffers are indexed by pair kind k (0,1,2); kinds with no products pass null
   prep_x_kernel<<<tile_grid(m), dim3(kTile, 8), 0, st>>>(x, m[0], m[1], m[2], t->R[0] ? t->x[0].as<__nv_bfloat16>() : nullptr,
                                           t->R[1] ? t->x[1].as<__nv_bfloat16>() : nullptr,
-                                          t->R[2] ? t->x[2].as<__nv_bfloat16>() : nullptr);
+                                          (t->R[2] || t->nt) ? t->x[2].as<__nv_bfloat16>() : nullptr);
   ctx->launches++;
   auto zero_split_outputs = [&]() {
     for (int k = 0; k < 3; ++k)
@@ -599,7 +666,7 @@ void attn_heff::apply_bf16(const double* x, double* y) {
       for (int rep = 0; rep < 3; ++rep) {
         if (t->split_any()) zero_split_outputs();
         ATTN_CHECK_CUDA(cudaEventRecord(e0, st));
-        sandwich_tc_kernel<<<t->grid, kThreads, t->smem, st>>>(t->maps, t->prm);
+        sandwich_tc_kernel<false><<<t->grid, kThreads, t->smem, st>>>(t->maps, t->prm);
         ATTN_CHECK_CUDA(cudaEventRecord(e1, st));
         ATTN_CHECK_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -626,29 +693,45 @@ void attn_heff::apply_bf16(const double* x, double* y) {
       if (has_hint[s]) fl += 2.0 * m[s] * V;
     if (t->split_any()) zero_split_outputs();
     ctx->prof_begin(0);
-    sandwich_tc_kernel<<<t->grid, kThreads, t->smem, st>>>(t->maps, t->prm);
+    sandwich_tc_kernel<false><<<t->grid, kThreads, t->smem, st>>>(t->maps, t->prm);
     ctx->prof_end(0, fl);
     ctx->launches++;
   }
-  combine_kernel<<<tile_grid(m), dim3(kTile, 8), 0, st>>>(y, m[0], m[1], m[2], t->R[0] ? t->y[0].as<float>() : nullptr,
+  if (t->nt > 0) {
+    // three-link products, one chunk of products at a time: W = x x_2 C_r on the
+    // TN GEMM, then Y01[c] += A_r W_r[c] B_r^T on the per-product kernel
+    const int P = m[0], Q = m[1], S = m[2];
+    if (!t->R[0]) ATTN_CHECK_CUDA(cudaMemsetAsync(t->y[0].p, 0, sizeof(float) * (size_t)V, st));
+    for (int r0 = 0; r0 < t->nt; r0 += t->tchunk) {
+      const int Rc = std::min(t->tchunk, t->nt - r0);
+      TnOperand A;  // x as [a b][c]: rows P Q, K = S
+      A.p = t->x[2].as<__nv_bfloat16>(); A.K = S; A.rows = P * Q; A.batches = 1; A.ld = S; A.bstride = 0;
+      TnOperand B;  // C_r as [r][c][c']
+      B.p = t->t2.as<__nv_bfloat16>() + (long)r0 * S * S; B.K = S; B.rows = S; B.batches = Rc; B.ld = S;
+      B.bstride = (long)S * S;
+      TnParams g;
+      g.M = P * Q; g.N = S; g.K = S; g.Bhi = Rc; g.Blo = 1; g.a_bhi = 0; g.b_bhi = 1;
+      g.C = t->w.p; g.c_type = 1; g.c_rs = 1; g.c_cs = (long)P * Q; g.c_bhi = V;
+      tn_gemm_bf16(ctx, A, B, g, t->err);
+      KindParams& kp = t->tprm.kind[0];
+      kp.R = Rc;
+      const int pairs = (S + 1) / 2;
+      const int f = std::max(1, std::min((ctx->num_sms + pairs - 1) / pairs, Rc / 8));
+      kp.rsplit = f;
+      const int grid = pairs * f;
+      TcMaps mp = t->tmaps;
+      encode_map(&mp.a[0], t->t0.as<__nv_bfloat16>() + (long)r0 * P * P, P, P, Rc, 128);
+      encode_map(&mp.b[0], t->t1.as<__nv_bfloat16>() + (long)r0 * Q * Q, Q, Q, Rc, 128);
+      ctx->prof_begin(0);
+      sandwich_tc_kernel<true><<<grid, kThreads, t->smem, st>>>(mp, t->tprm);
+      ctx->prof_end(0, (double)Rc * 2.0 * (P + Q) * V);
+      ctx->launches++;
+    }
+  }
+  combine_kernel<<<tile_grid(m), dim3(kTile, 8), 0, st>>>(y, m[0], m[1], m[2],
+                                           (t->R[0] || t->nt) ? t->y[0].as<float>() : nullptr,
                                            t->R[1] ? t->y[1].as<float>() : nullptr,
                                            t->R[2] ? t->y[2].as<float>() : nullptr);
   ctx->launches++;
   ATTN_CHECK_CUDA(cudaGetLastError());
-  if (ntrip > 0) {
-    // three-link products in FP64 on top of the tensor-core result
-    const int d[3] = {m[0], m[1], m[2]};
-    const long budget = 1L << 27;
-    const int chunk = (int)std::max<long>(1, std::min<long>(4096, budget / std::max<long>(V, 1)));
-    for (int r0 = 0; r0 < ntrip; r0 += chunk) {
-      const int R = std::min(chunk, ntrip - r0);
-      ctx->ws[0].reserve(sizeof(double) * (size_t)R * V);
-      ctx->ws[1].reserve(sizeof(double) * (size_t)R * V);
-      double* W1 = ctx->ws[0].as<double>();
-      double* W2 = ctx->ws[1].as<double>();
-      mode_product_f64(ctx, d, 2, tr[2].as<double>() + (long)r0 * m[2] * m[2], R, x, 0, W1, 0.0);
-      mode_product_f64(ctx, d, 1, tr[1].as<double>() + (long)r0 * m[1] * m[1], R, W1, V, W2, 0.0);
-      accumulate_slot_f64(ctx, d, 0, tr[0].as<double>() + (long)r0 * m[0] * m[0], R, W2, y);
-    }
-  }
 }

@@ -222,3 +222,71 @@ def test_mixed_precision_refinement_reaches_fp64_eigenpair():
     attn.attn_state_destroy(st)
     attn.attn_model_destroy(model)
     attn.attn_destroy(ctx)
+
+
+def _bound3(shape, counts, nt):
+    """Componentwise bound with three-link products: those terms see six BF16
+    roundings (x, C_r, W_r = x x_2 C_r, A_r, B_r, Z_r) and one more FP32 sum
+    over K = m2 in the slot-2 contraction."""
+    R = max(counts) + nt + 3
+    P = max(shape)
+    return (1 + U) ** 6 - 1 + (2 * P + R * P + 2) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("shape,counts,nt", [
+    ((128, 128, 128), (3, 2, 2), 5),
+    ((64, 64, 64), (0, 0, 0), 12),     # three-link products only
+    ((32, 48, 80), (5, 4, 3), 7),      # odd slice count, partial K blocks
+    ((16, 16, 128), (6, 0, 4), 9),     # no kind-(0, 2) products
+])
+def test_bf16_heff_three_link_products_within_rounding_bound(shape, counts, nt):
+    attn, ctx = lib_and_ctx()
+    h, pairs = _case(shape, counts, seed=5)
+    trip = tuple(random_operators(nt, m, 5, 60 + s) for s, m in enumerate(shape))
+    x = random_vector(shape, 11)
+    H = attn.attn_heff_create(ctx, shape, [dev(a) for a in h], {k: (dev(a), dev(b)) for k, (a, b) in pairs.items()},
+                              tuple(dev(t) for t in trip))
+    import torch
+    xd = dev(x)
+    yd = torch.full_like(xd, float("nan"))
+    for _ in range(2):  # the second call reuses the built state and must not double-count
+        attn.attn_heff_apply(H, xd, yd, attn.ATTN_BF16)
+    y = host(yd)
+    op = {KINDS[k]: v for k, v in pairs.items()}
+    y64 = heff_apply_ops(x, h, op, trip)
+    yabs = heff_apply_ops(np.abs(x), tuple(np.abs(a) for a in h),
+                          {k: (np.abs(a), np.abs(b)) for k, (a, b) in op.items()}, tuple(np.abs(t) for t in trip))
+    assert np.isfinite(y).all()
+    b = _bound3(shape, counts, nt)
+    viol = np.abs(y - y64) - b * yabs
+    assert viol.max() <= 1e-30, (float(viol.max()), b)
+    assert np.linalg.norm(y - y64) / np.linalg.norm(yabs) < U
+    attn.attn_heff_destroy(H)
+    attn.attn_destroy(ctx)
+
+
+def test_bf16_heff_three_link_products_full_size_sampled():
+    """[128]^3 with 300 three-link products next to the pair products, sampled entries."""
+    shape = (128, 128, 128)
+    counts, nt = (60, 30, 30), 300
+    attn, ctx = lib_and_ctx()
+    h, pairs = _case(shape, counts, seed=23)
+    trip = tuple(random_operators(nt, m, 23, 60 + s) for s, m in enumerate(shape))
+    x = random_vector(shape, 6)
+    H = attn.attn_heff_create(ctx, shape, [dev(a) for a in h], {k: (dev(a), dev(b)) for k, (a, b) in pairs.items()},
+                              tuple(dev(t) for t in trip))
+    import torch
+    xd = dev(x)
+    yd = torch.empty_like(xd)
+    attn.attn_heff_apply(H, xd, yd, attn.ATTN_BF16)
+    y = host(yd)
+    op = {KINDS[k]: v for k, v in pairs.items()}
+    rng = np.random.default_rng(2)
+    idx = [tuple(int(v) for v in rng.integers(0, 128, 3)) for _ in range(4)]
+    ref = heff_sample_ops(x, idx, h, op, trip)
+    absref = heff_sample_ops(np.abs(x), idx, tuple(np.abs(a) for a in h),
+                             {k: (np.abs(a), np.abs(b)) for k, (a, b) in op.items()}, tuple(np.abs(t) for t in trip))
+    got = np.array([y[i] for i in idx])
+    assert np.all(np.abs(got - ref) <= _bound3(shape, counts, nt) * absref)
+    attn.attn_heff_destroy(H)
+    attn.attn_destroy(ctx)
