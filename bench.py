@@ -311,6 +311,86 @@ def run_sweeps(args):
     print(json.dumps(line), flush=True)
 
 
+def run_converge(args):
+    """Converged energies under a frozen disentangler layer: one FP64 prefix of aTTN
+    sweeps (S_TTN = 1, then disentangler updates), after which every precision arm
+    starts from that identical state and H' and sweeps the TTN until the energy
+    changes by <= 1e-8 per site; final energies are compared with the FP64 arm's."""
+    import torch
+    from __graft_entry__ import build
+    from inputs import raw_tree_tensors
+    from paper_2507_21236_gb300 import attn
+
+    build()
+    Ls, ms, h = args.sweep_L, args.sweep_m, H_FIELD
+    n = Ls * Ls
+    raw = raw_tree_tensors(tree_shapes(n, ms), 0)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    # FP64 prefix: sweep 1 without disentanglers, then args.prefix - 1 sweeps with updates
+    ctx = attn.attn_create(attn.attn_config_default(), stream)
+    model = attn.attn_model_tfim(ctx, Ls, h)
+    st = attn.attn_state_create(ctx, model, ms, raw)
+    n_de = attn.attn_de_place(st, n // 4)
+    t0 = time.perf_counter()
+    prefix_e = [attn.attn_sweep(st) / n for _ in range(args.prefix)]
+    prefix_s = time.perf_counter() - t0
+    nn, centre, _ = attn.attn_state_info(st)
+    tensors = [attn.attn_node_get(st, i) for i in range(nn)]
+    us = [attn.attn_de_get(st, k) for k in range(n_de)]
+    attn.attn_state_destroy(st)
+    attn.attn_model_destroy(model)
+    attn.attn_destroy(ctx)
+
+    arms = {"f64": {}, "mixed_k3": {"matvec_dtype": attn.ATTN_BF16, "refine_steps": 3, "refine_inner": 16},
+            "mixed": {"matvec_dtype": attn.ATTN_BF16, "refine_steps": 8, "refine_inner": 16, "refine_tol": 1e-10}}
+    out = {}
+    for name, kv in arms.items():
+        cfg = attn.attn_config_default()
+        for k, v in kv.items():
+            setattr(cfg, k, v)
+        ctx = attn.attn_create(cfg, stream)
+        model = attn.attn_model_tfim(ctx, Ls, h)
+        st = attn.attn_state_create(ctx, model, ms, raw)
+        assert attn.attn_de_place(st, n // 4) == n_de
+        for k, u in enumerate(us):
+            attn.attn_de_set(st, k, u)
+        attn.attn_map_hamiltonian(st)
+        attn.attn_move_centre(st, centre)
+        for i, t in enumerate(tensors):
+            attn.attn_node_set(st, i, t)
+        es = [attn.attn_energy(st) / n]
+        ts = []
+        conv = None
+        for s in range(args.max_sweeps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            es.append(attn.attn_ttn_sweep(st) / n)
+            ts.append(time.perf_counter() - t0)
+            if abs(es[-1] - es[-2]) <= 1e-8:
+                conv = s + 1
+                break
+        out[name] = {"start_energy_per_site": es[0], "energies_per_site": es[1:], "sweep_s": ts,
+                     "sweeps_to_1e-8": conv, "time_to_1e-8_s": sum(ts) if conv else None}
+        attn.attn_state_destroy(st)
+        attn.attn_model_destroy(model)
+        attn.attn_destroy(ctx)
+    ref = out["f64"]["energies_per_site"][-1]
+    line = {"metric": "time to dE/site<=1e-8 under a frozen disentangler layer, mixed vs FP64", "unit": "s",
+            "value": out["mixed_k3"]["time_to_1e-8_s"], "higher_is_better": False,
+            "f64_value": out["f64"]["time_to_1e-8_s"],
+            "final_energy_per_site_minus_f64": {k: out[k]["energies_per_site"][-1] - ref for k in ("mixed_k3", "mixed")},
+            "config": {"workload": f"tfim{Ls}x{Ls}_m{ms}_converge", "L": Ls, "m": ms, "h": h, "n_de": n_de,
+                       "prefix": f"{args.prefix} FP64 aTTN sweeps (S_TTN = 1, then disentangler updates), "
+                                 f"{prefix_s:.1f} s, E/site {prefix_e}",
+                       "lanczos_depth": 20,
+                       "mixed_k3": "bf16 Lanczos + 3 FP64 Rayleigh-Ritz corrections from 16-step bf16 CG "
+                                   "Jacobi-Davidson solves (library default)",
+                       "mixed": "bf16 Lanczos + <= 8 such corrections, until theta moves by < 1e-10 |theta|"},
+            "runs": out}
+    print(json.dumps(line), flush=True)
+
+
 # (name, model, L, m, coupling): the matvec benchmark shapes of every configuration
 NODE_CONFIGS = [("C2", "tfim", 8, 32, 3.04), ("C3", "tfim", 16, 64, 3.04), ("C3", "tfim", 16, 128, 3.04),
                 ("C4", "heis", 16, 64, 1.0), ("C4", "heis", 16, 128, 1.0), ("C5", "tfim", 32, 128, 3.04)]
@@ -426,10 +506,11 @@ def run_nodes(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="matvec", choices=["matvec", "sweep", "nodes"])
+    ap.add_argument("--mode", default="matvec", choices=["matvec", "sweep", "nodes", "converge"])
     ap.add_argument("--sweep-L", type=int, default=16)
     ap.add_argument("--sweep-m", type=int, default=32)
     ap.add_argument("--max-sweeps", type=int, default=30)
+    ap.add_argument("--prefix", type=int, default=3, help="FP64 aTTN sweeps before the frozen-layer runs")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
@@ -442,6 +523,8 @@ def main():
         return run_sweeps(args)
     if args.mode == "nodes":
         return run_nodes(args)
+    if args.mode == "converge":
+        return run_converge(args)
     args.warmup = max(args.warmup, 3)
 
     import torch

@@ -71,6 +71,7 @@ struct attn_ctx {
   attn::DevBuf ws[4];
   attn::DevBuf scal;      // small device scalars
   attn::DevBuf partials;  // reduction partials (fixed size, allocated at creation)
+  attn::DevBuf gsplit_ws; // partial outputs of FP64 GEMMs whose reduction is split over CTA groups
   // Optional per-kernel timing (attn_profile_enable): event pairs around launches.
   bool prof_on = false;
   struct ProfRec {
@@ -112,6 +113,10 @@ struct GemmF64 {
   double* C = nullptr;
   long cM = 0, cN = 0, cBhi = 0, cBlo = 0;
   double alpha = 1.0, beta = 0.0;
+  // split of the G reduction over gsplit CTA groups: group s sums its share of G
+  // into C + s * cS (set by gemm_f64 when the output tiles alone underfill the GPU)
+  int gsplit = 1;
+  long cS = 0;
 };
 void gemm_f64(attn_ctx* ctx, const GemmF64& g);
 // The same kernels launched on a bare stream (no context, no allocation).

@@ -10,7 +10,10 @@
 // loads pick the coalesced mapping from the unit stride of each operand. The
 // tile is 32 or 64 wide in each direction, chosen from M and N: the mode
 // products of link dimension 32 are batches of 32 x 32 GEMMs, which a 64 x 64
-// tile would compute at a quarter of its width.
+// tile would compute at a quarter of its width. A GEMM whose output tiles do not
+// fill one wave of resident CTAs (the product-summing stage at m = 64 has 64)
+// splits its G reduction over CTA groups; the partial outputs are summed in a
+// fixed order by a second kernel, so results do not depend on scheduling.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,17 +37,19 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g) {
   const long nb = (long)g.Bhi * g.Blo;
   const bool a_kfast = (g.aK == 1);
   const bool b_nfast = (g.bN == 1);
-  for (long bz = blockIdx.z; bz < nb; bz += gridDim.z) {
-    const long bh = bz / g.Blo, bl = bz % g.Blo;
+  for (long bz = blockIdx.z; bz < nb * g.gsplit; bz += gridDim.z) {
+    const long sp = bz / nb, bb = bz % nb;
+    const long bh = bb / g.Blo, bl = bb % g.Blo;
     const double* Ab = g.A + bh * g.aBhi + bl * g.aBlo;
     const double* Bb = g.B + bh * g.bBhi + bl * g.bBlo;
-    double* Cb = g.C + bh * g.cBhi + bl * g.cBlo;
+    double* Cb = g.C + sp * g.cS + bh * g.cBhi + bl * g.cBlo;
+    const int ga = (int)(sp * g.G / g.gsplit), gb = (int)((sp + 1) * g.G / g.gsplit);
     double acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
-    for (int gg = 0; gg < g.G; ++gg) {
+    for (int gg = ga; gg < gb; ++gg) {
       const double* Ag = Ab + gg * g.aG;
       const double* Bg = Bb + gg * g.bG;
       for (int k0 = 0; k0 < g.K; k0 += BK) {
@@ -93,6 +98,20 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g) {
         *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
       }
     }
+  }
+}
+
+// C = beta C + alpha sum_s P[s] over the dense partials P[gsplit][batch][M][N].
+__global__ void split_reduce_kernel(GemmF64 g, const double* __restrict__ P) {
+  const long mn = (long)g.M * g.N, per = (long)g.Bhi * g.Blo * mn;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < per; e += (long)gridDim.x * blockDim.x) {
+    const long b = e / mn, r = e % mn;
+    const long i = r / g.N, j = r % g.N;
+    double s = 0.0;
+    for (int sp = 0; sp < g.gsplit; ++sp) s += P[sp * per + e];
+    double* c = g.C + (b / g.Blo) * g.cBhi + (b % g.Blo) * g.cBlo + i * g.cM + j * g.cN;
+    const double v = g.alpha * s;
+    *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
   }
 }
 
@@ -166,7 +185,7 @@ inline int grid_for(size_t n, int threads = 256, int cap = 4096) {
 cudaError_t launch_gemm(cudaStream_t stream, const GemmF64& g) {
   const bool sm = g.M <= 32, sn = g.N <= 32;
   const int bm = sm ? 32 : 64, bn = sn ? 32 : 64;
-  dim3 grid((g.N + bn - 1) / bn, (g.M + bm - 1) / bm, (unsigned)std::min<long>((long)g.Bhi * g.Blo, 65535));
+  dim3 grid((g.N + bn - 1) / bn, (g.M + bm - 1) / bm, (unsigned)std::min<long>((long)g.Bhi * g.Blo * g.gsplit, 65535));
   if (grid.y > 65535) return cudaErrorInvalidValue;
   if (sm && sn) gemm_f64_kernel<32, 32><<<grid, NT, 0, stream>>>(g);
   else if (sm) gemm_f64_kernel<32, 64><<<grid, NT, 0, stream>>>(g);
@@ -175,13 +194,58 @@ cudaError_t launch_gemm(cudaStream_t stream, const GemmF64& g) {
   return cudaGetLastError();
 }
 
+// Resident CTAs per SM of the tile shape launch_gemm picks for g (queried once per shape).
+static int resident_ctas(const GemmF64& g) {
+  static int occ[4] = {0, 0, 0, 0};
+  const int v = (g.M <= 32 ? 2 : 0) + (g.N <= 32 ? 1 : 0);
+  if (!occ[v]) {
+    cudaError_t e;
+    if (v == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[v], gemm_f64_kernel<32, 32>, NT, 0);
+    else if (v == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[v], gemm_f64_kernel<32, 64>, NT, 0);
+    else if (v == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[v], gemm_f64_kernel<64, 32>, NT, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[v], gemm_f64_kernel<64, 64>, NT, 0);
+    ATTN_CHECK_CUDA(e);
+    occ[v] = std::max(occ[v], 1);
+  }
+  return occ[v];
+}
+
 void gemm_f64(attn_ctx* ctx, const GemmF64& g) {
   if (g.M <= 0 || g.N <= 0 || g.Bhi <= 0 || g.Blo <= 0) return;
   ATTN_REQUIRE((g.M + 31) / 32 <= 65535, ATTN_EUNSUPPORTED, "GEMM M too large");
+  const double fl = 2.0 * g.M * g.N * (double)g.K * g.G * g.Bhi * g.Blo;
+  const int bm = g.M <= 32 ? 32 : 64, bn = g.N <= 32 ? 32 : 64;
+  const long nb = (long)g.Bhi * g.Blo;
+  const long tiles = (long)((g.N + bn - 1) / bn) * ((g.M + bm - 1) / bm) * nb;
+  const long slots = (long)std::max(ctx->num_sms, 1) * resident_ctas(g);
+  // split the G reduction when the output tiles fill less than half a wave: as many
+  // groups as keep the whole grid within one wave of resident CTAs
+  const int ks = (g.G >= 2 && 2 * tiles <= slots) ? (int)std::min<long>(g.G, slots / tiles) : 1;
   ctx->prof_begin(1);
-  ATTN_CHECK_CUDA(launch_gemm(ctx->stream, g));
-  ctx->prof_end(1, 2.0 * g.M * g.N * (double)g.K * g.G * g.Bhi * g.Blo);
-  ctx->launches++;
+  if (ks > 1) {
+    const long per = nb * g.M * g.N;
+    ctx->gsplit_ws.reserve(sizeof(double) * (size_t)ks * per);
+    GemmF64 p = g;
+    p.C = ctx->gsplit_ws.as<double>();
+    p.cN = 1;
+    p.cM = g.N;
+    p.cBlo = (long)g.M * g.N;
+    p.cBhi = (long)g.Blo * g.M * g.N;
+    p.cS = per;
+    p.gsplit = ks;
+    p.alpha = 1.0;
+    p.beta = 0.0;
+    ATTN_CHECK_CUDA(launch_gemm(ctx->stream, p));
+    GemmF64 r = g;
+    r.gsplit = ks;
+    split_reduce_kernel<<<grid_for((size_t)per), 256, 0, ctx->stream>>>(r, p.C);
+    ctx->launches += 2;
+  } else {
+    ATTN_CHECK_CUDA(launch_gemm(ctx->stream, g));
+    ctx->launches++;
+  }
+  ctx->prof_end(1, fl);
+  ATTN_CHECK_CUDA(cudaGetLastError());
 }
 
 cudaError_t gemm_f64_stream(cudaStream_t stream, const GemmF64& g) {

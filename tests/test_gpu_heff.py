@@ -38,6 +38,7 @@ def _oracle_pairs(pairs):
     ((16, 16, 32), (20, 10, 10), 3),
     ((100, 72, 130), (7, 5, 6), 2),   # ragged, several 64-wide tiles
     ((32, 32, 32), (120, 40, 40), 4),
+    ((64, 64, 64), (40, 20, 20), 3),  # product sums split over CTA groups (64 output tiles)
 ])
 def test_explicit_heff_f64_matches_oracle(shape, counts, ntrip):
     attn, ctx = lib_and_ctx()
