@@ -87,7 +87,11 @@ typedef struct {
   int use_graphs;           /* attn_eigsolve replays a captured CUDA graph of the low-precision Lanczos (0) */
   int refine_inner;         /* conjugate-gradient steps of the low-precision H_eff per correction, solving the
                                Jacobi-Davidson correction equation; 0 = the residual itself (16) */
-  int reserved[6];
+  int f64_split;            /* FP64 contractions of H_eff applications, renormalisation and disentangler
+                               environments as exact BF16 slice products on the tensor cores (Ozaki
+                               scheme, 47-bit operand slices): normwise error about (K + 2) 2^-46 of the
+                               operands' row scales, K the contraction length; QR stays on FP64 FMAs (0) */
+  int reserved[5];
 } attn_config;
 
 ATTN_API attn_status attn_config_default(attn_config* cfg);
@@ -108,7 +112,8 @@ ATTN_API attn_status attn_create(const attn_config* cfg, void* cuda_stream, attn
 ATTN_API attn_status attn_destroy(attn_ctx* ctx);
 ATTN_API attn_status attn_set_config(attn_ctx* ctx, const attn_config* cfg);
 ATTN_API attn_status attn_get_config(attn_ctx* ctx, attn_config* cfg);
-/* Block until all work enqueued by the context has finished. */
+/* Block until all work enqueued by the context has finished; ATTN_ETIMEOUT if a
+ * bounded wait in the split FP64 GEMM gave up meanwhile (its error word is then cleared). */
 ATTN_API attn_status attn_sync(attn_ctx* ctx);
 /* Number of library kernels launched by this context so far. */
 ATTN_API attn_status attn_kernel_launches(attn_ctx* ctx, uint64_t* count);
@@ -226,8 +231,9 @@ ATTN_API attn_status attn_heff_destroy(attn_heff* h);
 /* Counts: n_pair[3], n_triple, and the algorithmic FLOPs of one apply. */
 ATTN_API attn_status attn_heff_info(attn_heff* h, int n_pair[3], int* n_triple, double* flops);
 /* y_dev = H_eff x_dev (both DEVICE FP64 [m0][m1][m2], distinct buffers),
- * contractions in `dtype` (ATTN_F64 or ATTN_BF16 with FP32 accumulation).
- * Asynchronous on the context stream. */
+ * contractions in `dtype` (ATTN_F64 or ATTN_BF16 with FP32 accumulation; ATTN_F64
+ * runs its larger contractions as exact BF16 slice products when the context's
+ * f64_split is set). Asynchronous on the context stream. */
 ATTN_API attn_status attn_heff_apply(attn_heff* h, const double* x_dev, double* y_dev, attn_dtype dtype);
 /* Same with host buffers: copies x in, applies, copies y out (synchronous). */
 ATTN_API attn_status attn_heff_apply_host(attn_heff* h, const double* x_host, double* y_host, attn_dtype dtype);

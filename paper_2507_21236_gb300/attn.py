@@ -31,7 +31,7 @@ class attn_config(ctypes.Structure):
                 ("s_ttn", ctypes.c_int), ("matvec_dtype", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("refine_tol", ctypes.c_double),
                 ("use_graphs", ctypes.c_int), ("refine_inner", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("f64_split", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class attn_heff_desc(ctypes.Structure):

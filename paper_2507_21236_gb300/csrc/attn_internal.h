@@ -72,6 +72,9 @@ struct attn_ctx {
   attn::DevBuf scal;      // small device scalars
   attn::DevBuf partials;  // reduction partials (fixed size, allocated at creation)
   attn::DevBuf gsplit_ws; // partial outputs of FP64 GEMMs whose reduction is split over CTA groups
+  attn::DevBuf oz_ws[4];  // split-GEMM operand slices and row exponents (P slices, P exps, Q slices, Q exps)
+  attn::DevBuf oz_err;    // split-GEMM device error word
+  bool oz_err_init = false;
   // Optional per-kernel timing (attn_profile_enable): event pairs around launches.
   bool prof_on = false;
   struct ProfRec {
@@ -117,6 +120,8 @@ struct GemmF64 {
   // into C + s * cS (set by gemm_f64 when the output tiles alone underfill the GPU)
   int gsplit = 1;
   long cS = 0;
+  // the contraction may run as exact BF16 slice products when attn_config.f64_split is set
+  bool split_ok = false;
 };
 void gemm_f64(attn_ctx* ctx, const GemmF64& g);
 // The same kernels launched on a bare stream (no context, no allocation).

@@ -196,6 +196,7 @@ ATTN_API attn_status attn_sync(attn_ctx* ctx) {
   ATTN_TRY
   NEED(ctx, "ctx");
   ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  check_device_errors(ctx, nullptr);
   ATTN_CATCH
 }
 
@@ -677,6 +678,7 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
       *theta = f.theta;
       it += f.fp64_matvecs + f.lo_matvecs;
     }
+    check_device_errors(ctx, h);
     if (iters) *iters = it;
     return ATTN_OK;
   }
@@ -691,6 +693,7 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
     it += f.fp64_matvecs + f.lo_matvecs;
   }
   ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  check_device_errors(ctx, h);
   *theta = th;
   if (iters) *iters = it;
   ATTN_CATCH

@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "attn_internal.h"
+#include "ozaki.h"
 
 namespace attn {
 
@@ -214,6 +215,12 @@ void gemm_f64(attn_ctx* ctx, const GemmF64& g) {
   if (g.M <= 0 || g.N <= 0 || g.Bhi <= 0 || g.Blo <= 0) return;
   ATTN_REQUIRE((g.M + 31) / 32 <= 65535, ATTN_EUNSUPPORTED, "GEMM M too large");
   const double fl = 2.0 * g.M * g.N * (double)g.K * g.G * g.Bhi * g.Blo;
+  // marked contractions of at least ~1e8 FLOP run as exact BF16 slice products when
+  // enabled: GB300's FP64 FMA rate is a small fraction of its tensor-core rate
+  if (ctx->cfg.f64_split && g.split_ok && fl >= 1e8 && std::max(g.M, g.N) >= 32) {
+    gemm_f64_ozaki(ctx, g);
+    return;
+  }
   const int bm = g.M <= 32 ? 32 : 64, bn = g.N <= 32 ? 32 : 64;
   const long nb = (long)g.Bhi * g.Blo;
   const long tiles = (long)((g.N + bn - 1) / bn) * ((g.M + bm - 1) / bm) * nb;
@@ -264,6 +271,7 @@ void mode_product_f64(attn_ctx* ctx, const int d[3], int slot, const double* mat
   const long V = (long)d[0] * d[1] * d[2];
   const long ms = (long)d[slot] * d[slot];
   GemmF64 g;
+  g.split_ok = true;
   g.beta = beta;
   if (slot == 0) {
     // out_r[i, (bc)] = sum_j M_r[i, j] in_r[j, (bc)]

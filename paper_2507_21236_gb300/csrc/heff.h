@@ -56,6 +56,9 @@ namespace attn {
 void tc_release(attn_heff* h);
 bool tc_supported(const attn_heff* h);
 int tc_error(attn_heff* h);
+// Throws ATTN_ETIMEOUT when a bounded wait in a tensor-core kernel gave up (the
+// H_eff's tensor-core error word, if h is given, and the split FP64 GEMM's).
+void check_device_errors(attn_ctx* ctx, attn_heff* h);
 // y += sum_{r<R} A_r x_p W_r with W_r per-product tensors (stride V), FP64.
 void accumulate_slot_f64(attn_ctx* ctx, const int d[3], int p, const double* A, int R, const double* W, double* y);
 }  // namespace attn

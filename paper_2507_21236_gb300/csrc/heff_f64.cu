@@ -32,6 +32,7 @@ namespace attn {
 void accumulate_slot_f64(attn_ctx* ctx, const int d[3], int p, const double* A, int R, const double* W, double* y) {
   const long V = (long)d[0] * d[1] * d[2];
   GemmF64 g;
+  g.split_ok = true;
   g.beta = 1.0;
   g.G = R;
   if (p == 0) {

@@ -46,6 +46,7 @@
 
 #include "gemm_tc.h"
 #include "heff.h"
+#include "ozaki.h"
 #include "tc_ptx.h"
 
 namespace attn {
@@ -609,6 +610,13 @@ int tc_error(attn_heff* h) {
   ATTN_CHECK_CUDA(cudaStreamSynchronize(h->ctx->stream));
   if (e) ATTN_CHECK_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), h->ctx->stream));
   return e;
+}
+
+void check_device_errors(attn_ctx* ctx, attn_heff* h) {
+  const int et = h ? tc_error(h) : 0;
+  const int eo = ozaki_error(ctx);
+  ATTN_REQUIRE(et == 0 && eo == 0, ATTN_ETIMEOUT,
+               "a bounded wait in a tensor-core kernel gave up (code " + std::to_string(et ? et : eo) + ")");
 }
 
 }  // namespace attn

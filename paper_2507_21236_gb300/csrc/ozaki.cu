@@ -1,0 +1,491 @@
+// FP64-accurate GEMM on the BF16 tensor cores by operand splitting (the Ozaki
+// scheme: K. Ozaki, T. Ogita, S. Oishi, S. M. Rump, "Error-free transformations
+// of matrix multiplication by using fast routines of matrix multiplication and
+// its applications", Numer. Algorithms 59 (2012)).
+//
+// GB300 executes FP64 FMAs at about 1.2 TFLOP/s, three orders of magnitude
+// below its BF16 tensor rate, so the FP64 contractions of the method (the
+// renormalisation T^T (O (x) O) T of Fig. eff-op and the FP64 H_eff
+// applications of the residual corrections) can run faster as many exact BF16
+// products than as FP64 FMAs. For C = P Q^T (P: M x K, Q: N x K, FP64):
+//
+//  * every row of P (and of Q) is scaled by a power of two 2^-E so that its
+//    entries lie in (-1, 1), then written as six BF16 integers,
+//        p = 2^E sum_{s=1..6} n_s 2^(1-8s),  |n_s| <= 128,
+//    i.e. 7 + 5 x 8 = 47 significant bits (relative residual <= 2^-48);
+//  * the slice pairs (s, t) with s + t <= 7 (21 of 36; the rest lie below
+//    2^-46 of the row scales) are multiplied on the tensor cores. Pairs on
+//    one diagonal c = s + t share the scale 2^(2-8c) and accumulate into one
+//    TMEM accumulator. Every product is an integer below 2^14 in magnitude and
+//    a diagonal has at most 6 pairs, so over one 64-wide K block every partial
+//    sum stays below 6 * 2^14 * 64 < 2^23 and the FP32 accumulation is exact;
+//  * after each K block the epilogue folds the six diagonals into an int64
+//    fixed-point sum per output element (unit 2^-46 of the row scales; the
+//    finest diagonal is rounded to that unit), and converts to FP64 once.
+//
+// The error is normwise: |C - C~|_ij <= about (K + 2) 2^-46 2^(E_i + E_j),
+// with 2^E_i and 2^E_j at most twice the largest |entry| of row i of P and of
+// row j of Q. K per launch is limited to 65536 so the int64 sum cannot overflow.
+//
+// Kernel: one CTA per 128 x 64 output tile of one batch entry. Warp 0 is the
+// TMA producer, warp 1 allocates TMEM and issues the MMAs, warps 2-17 read the
+// diagonals (four warps per 32-lane quarter w % 4, 16 columns each). The six Q slices
+// of a K block (48 KB) are double-buffered; the P slices stream through a ring
+// of eight 16 KB stages. All waits are bounded; on a timeout the CTA records an
+// error code, stops issuing, drains its copies and frees TMEM.
+#include <algorithm>
+#include <climits>
+
+#include "ozaki.h"
+#include "tc_ptx.h"
+
+namespace attn {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kSlices = 6;
+constexpr int kDiags = 6;               // c = s + t = 2 .. 7
+constexpr int kOzThreads = 576;         // 2 role warps + 16 epilogue warps
+constexpr int kQRows = 64;              // output tile columns (rows of Q)
+constexpr int kPBytes = 128 * 128;      // one 128-row x 64-wide BF16 K block of one P slice
+constexpr int kQBytes = kQRows * 128;   // one 64-row K block of one Q slice
+constexpr int kPStages = 8;
+constexpr int kQBufBytes = kSlices * kQBytes;
+constexpr int kEmptyRow = -2000;        // exponent of an all-zero row
+constexpr int kUnitExp = 46;            // fixed-point unit 2^-46 of the row scales
+
+struct OzParams {
+  int M, N, nkb;           // rows of P, rows of Q, 64-wide K blocks
+  int Bhi, Blo;            // batch entries b = bhi * Blo + blo
+  int p_hi, p_lo, q_hi, q_lo;  // sliced-operand batch index = bhi * x_hi + blo * x_lo
+  const int* EP;           // [batches of P][M] row exponents
+  const int* EQ;           // [batches of Q][N]
+  double* C;
+  long c_rs, c_cs, c_bhi, c_blo;
+  double alpha, beta;
+  long batch_offset;
+  int* err;
+};
+
+struct OzMaps {
+  CUtensorMap p, q;  // [batches * 6][rows][Kpad] BF16, boxes {64, 128, 1} and {64, 64, 1}
+};
+
+__global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_constant__ OzMaps maps, OzParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t sQ = base;                     // two buffers of six Q slices
+  const uint32_t sP = base + 2 * kQBufBytes;    // ring of P slice K blocks
+  const uint32_t sBar = sP + kPStages * kPBytes;
+  enum {
+    QFULL = 0,
+    QEMPTY = 2,
+    PFULL = 4,
+    PEMPTY = 4 + kPStages,
+    DFULL = 4 + 2 * kPStages,   // the K block's diagonals are complete in TMEM
+    DEMPTY = 5 + 2 * kPStages,  // the epilogue has read them
+    MDONE = 6 + 2 * kPStages,   // every MMA of the CTA has completed
+    NBAR = 7 + 2 * kPStages
+  };
+  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + (sBar - base));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBAR);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto bar = [&](int i) { return sBar + 8u * (uint32_t)i; };
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long b = (long)blockIdx.z + p.batch_offset;
+  const int bhi = (int)(b / p.Blo), blo = (int)(b % p.Blo);
+  const int bp = bhi * p.p_hi + blo * p.p_lo, bq = bhi * p.q_hi + blo * p.q_lo;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * kQRows;
+  const int nkb = p.nkb;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(bar(QFULL + i), 1);
+      mbar_init(bar(QEMPTY + i), 1);
+    }
+    for (int i = 0; i < kPStages; ++i) {
+      mbar_init(bar(PFULL + i), 1);
+      mbar_init(bar(PEMPTY + i), 1);
+    }
+    mbar_init(bar(DFULL), 1);
+    mbar_init(bar(DEMPTY), 16);
+    mbar_init(bar(MDONE), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;  // diagonal d = c - 2 in columns 64 d .. 64 d + 63
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer: per K block the six Q slices, then the six P slices
+    int pst = 0, pissued = 0;
+    uint32_t pph = 0;
+    int qissued = 0;
+    bool ok = true;
+    for (int kb = 0; ok && kb < nkb; ++kb) {
+      const int qb = kb & 1;
+      if (kb >= 2 && !mbar_wait(bar(QEMPTY + qb), ((kb >> 1) - 1) & 1, p.err, 61, abort_flag)) break;
+      mbar_expect_tx(bar(QFULL + qb), (uint32_t)kQBufBytes);
+      for (int s = 0; s < kSlices; ++s)
+        tma_load_3d(sQ + qb * kQBufBytes + s * kQBytes, &maps.q, 64 * kb, n0, bq * kSlices + s, bar(QFULL + qb));
+      qissued = kb + 1;
+      for (int s = 0; s < kSlices; ++s) {
+        if (pissued >= kPStages && !mbar_wait(bar(PEMPTY + pst), pph ^ 1u, p.err, 62, abort_flag)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(bar(PFULL + pst), (uint32_t)kPBytes);
+        tma_load_3d(sP + pst * kPBytes, &maps.p, 64 * kb, m0, bp * kSlices + s, bar(PFULL + pst));
+        ++pissued;
+        if (++pst == kPStages) { pst = 0; pph ^= 1u; }
+      }
+    }
+    // drain: every issued copy must land before the CTA exits
+    for (int kb = (qissued > 2 ? qissued - 2 : 0); kb < qissued; ++kb) {
+      long long t0 = clock64();
+      while (!mbar_try_wait(bar(QFULL + (kb & 1)), (kb >> 1) & 1) && clock64() - t0 < kWaitCycles) {}
+    }
+    for (int q = (pissued > kPStages ? pissued - kPStages : 0); q < pissued; ++q) {
+      long long t0 = clock64();
+      while (!mbar_try_wait(bar(PFULL + q % kPStages), (q / kPStages) & 1) && clock64() - t0 < kWaitCycles) {}
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issue: diagonal d accumulates the pairs (s, t) with s + t = d (0-based slices)
+    const uint32_t id = idesc_bf16(128, kQRows);
+    const uint64_t dP0 = sw128_desc(sP), dQ0 = sw128_desc(sQ);
+    int pst = 0;
+    uint32_t pph = 0;
+    bool ok = true;
+    for (int kb = 0; ok && kb < nkb; ++kb) {
+      const int qb = kb & 1;
+      // the diagonals hold the previous K block until the epilogue has read them
+      if (kb > 0 && !mbar_wait(bar(DEMPTY), (kb - 1) & 1, p.err, 63, abort_flag)) break;
+      if (!mbar_wait(bar(QFULL + qb), (kb >> 1) & 1, p.err, 64, abort_flag)) break;
+      fence_after();
+      uint32_t touched = 0;
+      for (int s = 0; s < kSlices; ++s) {
+        if (!mbar_wait(bar(PFULL + pst), pph, p.err, 65, abort_flag)) { ok = false; break; }
+        fence_after();
+        const uint64_t dP = dP0 + (uint64_t)(pst * (kPBytes >> 4));
+        for (int t = 0; s + t < kDiags; ++t) {
+          const int d = s + t;
+          const uint64_t dQ = dQ0 + (uint64_t)((qb * kQBufBytes + t * kQBytes) >> 4);
+          mma4_ss(tmem + 64u * (uint32_t)d, dP, dQ, id, (touched >> d) & 1u);
+          touched |= 1u << d;
+        }
+        mma_commit(bar(PEMPTY + pst));
+        if (++pst == kPStages) { pst = 0; pph ^= 1u; }
+      }
+      if (!ok) break;
+      mma_commit(bar(QEMPTY + qb));
+      mma_commit(bar(DFULL));
+    }
+    mma_commit(bar(MDONE));
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar(MDONE), 0) && clock64() - t0 < kWaitCycles) {}
+  } else if (warp >= 2) {
+    // ---- epilogue: lane quarter q4, columns 16 h .. 16 h + 15 of the tile
+    const int q4 = warp & 3, h = (warp - 2) >> 2;
+    const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
+    long long acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0;
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      // warp-uniform: the TMEM loads below are .sync.aligned
+      if (!__all_sync(0xffffffffu, mbar_wait(bar(DFULL), kb & 1, p.err, 66, abort_flag))) { ok = false; break; }
+      fence_after();
+#pragma unroll
+      for (int d = 0; d < kDiags; ++d) {
+        float v[16];
+        tmem_ld16(tmem + lane_off + 64u * (uint32_t)d + 16u * (uint32_t)h, v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const long long x = (long long)__float2int_rn(v[c]);  // exact: |v| < 2^23
+          if (d < kDiags - 1) acc[c] += x << (8 * (kDiags - 2 - d));
+          else acc[c] += (x + 128) >> 8;  // the finest diagonal, rounded to the unit
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(DEMPTY));
+    }
+    const int i = m0 + q4 * 32 + lane;
+    if (ok && i < p.M) {
+      const int ep = p.EP[(long)bp * p.M + i];
+      const long cbase = (long)bhi * p.c_bhi + (long)blo * p.c_blo + (long)i * p.c_rs;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int j = n0 + 16 * h + c;
+        if (j < p.N) {
+          const int e = ep + p.EQ[(long)bq * p.N + j] - kUnitExp;
+          const double v = p.alpha * ldexp((double)acc[c], e);
+          double* cp = p.C + cbase + (long)j * p.c_cs;
+          *cp = (p.beta == 0.0) ? v : fma(p.beta, *cp, v);
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// ------------------------------------------------------------ slicing kernels
+// Operand element (batch bh, bl; row r; k' = g K + k) of a strided FP64 view.
+__device__ __forceinline__ long oz_offset(const OzView& v, int bh, int bl, long r, long kk) {
+  const long g = kk / v.K, k = kk - g * v.K;
+  return (long)bh * v.sBhi + (long)bl * v.sBlo + r * v.sR + g * v.sG + k * v.sK;
+}
+
+constexpr int kT = 32;  // 32 rows x 32 k per tile, 32 x 8 threads
+
+__global__ void fill_int_kernel(int* p, long n, int v) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// Binary exponent e of a finite nonzero double (|x| = f 2^e, f in [0.5, 1)) from its
+// bits: integer instructions only (the FP64 pipe is the scarce unit on this GPU).
+__device__ __forceinline__ int exp_bits(long long b) {
+  const int ef = (int)((b >> 52) & 0x7FF);
+  if (ef) return ef - 1022;
+  const unsigned long long m = (unsigned long long)b & 0xFFFFFFFFFFFFFull;  // subnormal
+  return -1022 - (__clzll(m) - 12);
+}
+
+// E[batch][row] = max over k' of the binary exponent of |entry| (|entry| < 2^E).
+// Lanes walk k when k is the unit stride (each warp then owns four rows of the
+// tile), rows otherwise; every shuffle runs on the whole warp.
+__global__ void oz_exponent_kernel(OzView v, int* E) {
+  __shared__ int sh[8][kT + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long r0 = (long)blockIdx.y * kT;
+  const int batch = blockIdx.z, bh = batch / v.nblo, bl = batch % v.nblo;
+  const long Kt = (long)v.K * v.G;
+  const bool kfast = (v.sK == 1 && v.sR != 1);
+  int em[kT / 8];
+#pragma unroll
+  for (int j = 0; j < kT / 8; ++j) em[j] = kEmptyRow;
+  for (long k0 = (long)blockIdx.x * kT; k0 < Kt; k0 += (long)gridDim.x * kT) {
+#pragma unroll
+    for (int j = 0; j < kT / 8; ++j) {
+      const int i = ty + 8 * j;
+      const long r = kfast ? r0 + i : r0 + tx, k = kfast ? k0 + tx : k0 + i;
+      if (r < v.rows && k < Kt) {
+        const long long b = __double_as_longlong(v.p[oz_offset(v, bh, bl, r, k)]);
+        if (b & 0x7FFFFFFFFFFFFFFFll) em[j] = max(em[j], exp_bits(b));
+      }
+    }
+  }
+  if (kfast) {
+#pragma unroll
+    for (int j = 0; j < kT / 8; ++j) {
+      int m = em[j];
+      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      const long r = r0 + ty + 8 * j;
+      if (tx == 0 && r < v.rows && m > kEmptyRow) atomicMax(&E[(long)batch * v.rows + r], m);
+    }
+    return;
+  }
+  int m = em[0];
+#pragma unroll
+  for (int j = 1; j < kT / 8; ++j) m = max(m, em[j]);
+  sh[ty][tx] = m;
+  __syncthreads();
+  if (ty == 0) {
+    for (int i = 1; i < 8; ++i) m = max(m, sh[i][tx]);
+    const long r = r0 + tx;
+    if (r < v.rows && m > kEmptyRow) atomicMax(&E[(long)batch * v.rows + r], m);
+  }
+}
+
+// S[batch][s][row][Kpad] = slice s of 2^-E[row] entry, zero for k' >= K G. The
+// entry becomes the integer F = round(|x| 2^(47-E)) (|F| < 2^47, from the bits of
+// x, rounding half up), signed, then balanced base-256 digits from the bottom:
+// n_6 .. n_2 in [-128, 127], n_1 = the rest (|n_1| <= 128), F = sum_s n_s 2^(8(6-s)).
+__global__ void oz_slice_kernel(OzView v, const int* E, __nv_bfloat16* S, long Kpad) {
+  __shared__ long long t[kT][kT + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const long r0 = (long)blockIdx.y * kT, k0 = (long)blockIdx.x * kT;
+  const int batch = blockIdx.z, bh = batch / v.nblo, bl = batch % v.nblo;
+  const long Kt = (long)v.K * v.G;
+  const bool kfast = (v.sK == 1 && v.sR != 1);
+  for (int i = ty; i < kT; i += 8) {
+    const long r = kfast ? r0 + i : r0 + tx, k = kfast ? k0 + tx : k0 + i;
+    long long b = 0;
+    if (r < v.rows && k < Kt) b = __double_as_longlong(v.p[oz_offset(v, bh, bl, r, k)]);
+    if (kfast) t[i][tx] = b;
+    else t[tx][i] = b;
+  }
+  __syncthreads();
+  for (int i = ty; i < kT; i += 8) {
+    const long r = r0 + i, k = k0 + tx;
+    if (r >= v.rows || k >= Kpad) continue;
+    const long long b = t[i][tx];
+    const int e = E[(long)batch * v.rows + r];
+    long long F = 0;
+    if ((b & 0x7FFFFFFFFFFFFFFFll) && e != kEmptyRow) {
+      const int ef = (int)((b >> 52) & 0x7FF);
+      const long long mant = (b & 0xFFFFFFFFFFFFFll) | (ef ? (1ll << 52) : 0ll);
+      const int sh = (ef ? ef - 1075 : -1074) + 47 - e;  // |x| = mant 2^(ef - 1075)
+      if (sh >= 0) F = mant << sh;                       // < 2^47 since |x| < 2^e
+      else if (sh > -64) F = (sh == -63 ? 0ll : (mant + (1ll << (-sh - 1))) >> (-sh));
+      if (b < 0) F = -F;
+    }
+    __nv_bfloat16* out = S + ((long)batch * kSlices * v.rows + r) * Kpad + k;
+#pragma unroll
+    for (int s = kSlices - 1; s >= 1; --s) {
+      const int d = (int)(((F & 255) ^ 128) - 128);  // balanced digit in [-128, 127]
+      out[(long)s * v.rows * Kpad] = __int2bfloat16_rn(d);  // exact: |d| <= 128
+      F = (F - d) >> 8;
+    }
+    out[0] = __int2bfloat16_rn((int)F);
+  }
+}
+
+void encode_slices(CUtensorMap* map, const __nv_bfloat16* p, long Kpad, int rows, long nslices, int box_rows) {
+  cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows, (cuuint64_t)nslices};
+  cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)Kpad * rows * 2};
+  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = tensor_map_encoder()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(p), dims,
+                                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  ATTN_REQUIRE(r == CUDA_SUCCESS, ATTN_ECUDA, "cuTensorMapEncodeTiled failed for Ozaki slices");
+}
+
+int grid_cap(long n) { return (int)std::max<long>(1, std::min<long>(n, 65535)); }
+
+}  // namespace
+
+void ozaki_slice(attn_ctx* ctx, const OzView& v, long Kpad, DevBuf& slices, DevBuf& exps) {
+  const long nb = (long)v.nbhi * v.nblo;
+  ATTN_REQUIRE(nb <= 65535, ATTN_EUNSUPPORTED, "too many operand batches for the split GEMM");
+  slices.reserve(sizeof(__nv_bfloat16) * (size_t)(nb * kSlices * v.rows * Kpad));
+  exps.reserve(sizeof(int) * (size_t)(nb * v.rows));
+  cudaStream_t st = ctx->stream;
+  const long ne = nb * v.rows;
+  fill_int_kernel<<<(int)std::min<long>((ne + 255) / 256, 4096), 256, 0, st>>>(exps.as<int>(), ne, kEmptyRow);
+  const long Kt = (long)v.K * v.G;
+  const long rt = (v.rows + kT - 1) / kT;
+  ATTN_REQUIRE(rt <= 65535, ATTN_EUNSUPPORTED, "too many rows for the split GEMM");
+  dim3 blk(kT, 8);
+  // exponent pass: k tiles folded so that the grid stays modest
+  const long kt = (Kt + kT - 1) / kT;
+  dim3 ge((unsigned)std::min<long>(kt, std::max<long>(1, 8192 / std::max<long>(rt * nb, 1))), (unsigned)rt,
+          (unsigned)nb);
+  oz_exponent_kernel<<<ge, blk, 0, st>>>(v, exps.as<int>());
+  dim3 gs((unsigned)((Kpad + kT - 1) / kT), (unsigned)rt, (unsigned)nb);
+  ATTN_REQUIRE(gs.x <= 2147483647u, ATTN_EUNSUPPORTED, "K too large for the split GEMM");
+  oz_slice_kernel<<<gs, blk, 0, st>>>(v, exps.as<int>(), slices.as<__nv_bfloat16>(), Kpad);
+  ctx->launches += 3;
+  ATTN_CHECK_CUDA(cudaGetLastError());
+}
+
+// C = alpha sum_g A_g B_g + beta C of a GemmF64 through the split BF16 products.
+void gemm_f64_ozaki(attn_ctx* ctx, const GemmF64& g0) {
+  if (g0.M <= 0 || g0.N <= 0 || g0.Bhi <= 0 || g0.Blo <= 0) return;
+  // orientation: TMEM lanes are output rows, so the side whose C stride is 1 goes on
+  // the 128-row side (coalesced stores) unless it is much shorter than the other
+  bool swap = g0.N > g0.M;
+  if (std::min(g0.M, g0.N) >= 64) {
+    if (g0.cN == 1 && g0.cM != 1) swap = true;
+    else if (g0.cM == 1 && g0.cN != 1) swap = false;
+  }
+  OzView P, Q;
+  int M, N;
+  long c_rs, c_cs;
+  if (!swap) {
+    M = g0.M; N = g0.N;
+    P.p = g0.A; P.sR = g0.aM; P.sK = g0.aK; P.sG = g0.aG; P.sBhi = g0.aBhi; P.sBlo = g0.aBlo;
+    Q.p = g0.B; Q.sR = g0.bN; Q.sK = g0.bK; Q.sG = g0.bG; Q.sBhi = g0.bBhi; Q.sBlo = g0.bBlo;
+    c_rs = g0.cM; c_cs = g0.cN;
+  } else {
+    M = g0.N; N = g0.M;
+    P.p = g0.B; P.sR = g0.bN; P.sK = g0.bK; P.sG = g0.bG; P.sBhi = g0.bBhi; P.sBlo = g0.bBlo;
+    Q.p = g0.A; Q.sR = g0.aM; Q.sK = g0.aK; Q.sG = g0.aG; Q.sBhi = g0.aBhi; Q.sBlo = g0.aBlo;
+    c_rs = g0.cN; c_cs = g0.cM;
+  }
+  P.rows = M; Q.rows = N;
+  P.K = Q.K = g0.K;
+  P.nbhi = P.sBhi ? g0.Bhi : 1; P.nblo = P.sBlo ? g0.Blo : 1;
+  Q.nbhi = Q.sBhi ? g0.Bhi : 1; Q.nblo = Q.sBlo ? g0.Blo : 1;
+  // K per launch <= 65536 (int64 headroom): groups of G
+  const int gstep = std::max(1, (int)std::min<long>(g0.G, 65536L / std::max(g0.K, 1)));
+  ATTN_REQUIRE(g0.K <= 65536, ATTN_EUNSUPPORTED, "K above 65536 for the split GEMM");
+  const size_t smem = 1024 + 2 * (size_t)kQBufBytes + (size_t)kPStages * kPBytes + 256;
+  static bool attr = false;
+  if (!attr) {
+    ATTN_CHECK_CUDA(cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  ctx->oz_err.reserve(sizeof(int));
+  if (!ctx->oz_err_init) {
+    ATTN_CHECK_CUDA(cudaMemsetAsync(ctx->oz_err.p, 0, sizeof(int), ctx->stream));
+    ctx->oz_err_init = true;
+  }
+  const double fl = 2.0 * g0.M * g0.N * (double)g0.K * g0.G * g0.Bhi * g0.Blo;
+  ctx->prof_begin(3);
+  for (int ga = 0; ga < g0.G; ga += gstep) {
+    const int gn = std::min(gstep, g0.G - ga);
+    OzView p = P, q = Q;
+    p.p = P.p + (long)ga * P.sG;
+    q.p = Q.p + (long)ga * Q.sG;
+    p.G = q.G = gn;
+    const long Kt = (long)g0.K * gn;
+    const long Kpad = (Kt + 63) / 64 * 64;
+    ozaki_slice(ctx, p, Kpad, ctx->oz_ws[0], ctx->oz_ws[1]);
+    ozaki_slice(ctx, q, Kpad, ctx->oz_ws[2], ctx->oz_ws[3]);
+    OzMaps maps;
+    encode_slices(&maps.p, ctx->oz_ws[0].as<__nv_bfloat16>(), Kpad, M, (long)p.nbhi * p.nblo * kSlices, 128);
+    encode_slices(&maps.q, ctx->oz_ws[2].as<__nv_bfloat16>(), Kpad, N, (long)q.nbhi * q.nblo * kSlices, kQRows);
+    OzParams prm;
+    prm.M = M; prm.N = N; prm.nkb = (int)(Kpad / 64);
+    prm.Bhi = g0.Bhi; prm.Blo = g0.Blo;
+    prm.p_hi = P.sBhi ? p.nblo : 0; prm.p_lo = P.sBlo ? 1 : 0;
+    prm.q_hi = Q.sBhi ? q.nblo : 0; prm.q_lo = Q.sBlo ? 1 : 0;
+    prm.EP = ctx->oz_ws[1].as<int>();
+    prm.EQ = ctx->oz_ws[3].as<int>();
+    prm.C = g0.C; prm.c_rs = c_rs; prm.c_cs = c_cs; prm.c_bhi = g0.cBhi; prm.c_blo = g0.cBlo;
+    prm.alpha = g0.alpha;
+    prm.beta = ga == 0 ? g0.beta : 1.0;
+    prm.err = ctx->oz_err.as<int>();
+    const long total = (long)g0.Bhi * g0.Blo;
+    dim3 grid((unsigned)((N + kQRows - 1) / kQRows), (unsigned)((M + 127) / 128), 1);
+    ATTN_REQUIRE(grid.y <= 65535, ATTN_EUNSUPPORTED, "M too large for the split GEMM");
+    for (long off = 0; off < total; off += 65535) {
+      grid.z = (unsigned)grid_cap(total - off);
+      prm.batch_offset = off;
+      ozaki_gemm_kernel<<<grid, kOzThreads, smem, ctx->stream>>>(maps, prm);
+      ctx->launches++;
+    }
+  }
+  ctx->prof_end(3, fl);
+  ATTN_CHECK_CUDA(cudaGetLastError());
+}
+
+int ozaki_error(attn_ctx* ctx) {
+  if (!ctx->oz_err_init) return 0;
+  int e = 0;
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(&e, ctx->oz_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (e) ATTN_CHECK_CUDA(cudaMemsetAsync(ctx->oz_err.p, 0, sizeof(int), ctx->stream));
+  return e;
+}
+
+}  // namespace attn

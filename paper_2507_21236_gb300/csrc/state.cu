@@ -54,6 +54,7 @@ __global__ void gram_err_kernel(const double* G, int k, double* out) {
 void contract_tt(attn_ctx* ctx, const double* T, const int d[3], int t, const double* W, int R, double* out) {
   const long V = (long)d[0] * d[1] * d[2];
   GemmF64 g;
+  g.split_ok = true;
   g.M = g.N = d[t];
   g.Bhi = R;
   g.C = out; g.cM = d[t]; g.cN = 1; g.cBhi = (long)d[t] * d[t];
@@ -474,6 +475,7 @@ double attn_state::local_step(int n) {
       theta = refine_eig(ctx, mv64, mv_lo, v, V, cfg.refine_steps, cfg.refine_inner, cfg.refine_tol, rfw).theta;
       exact = true;
     }
+    check_device_errors(ctx, h);
     if (theta <= e_cur + 1e-14 * std::fabs(e_cur)) {
       std::swap(T[n], tmpT);
       invalidate_from(n);
