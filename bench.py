@@ -400,6 +400,54 @@ def run_converge(args):
     print(json.dumps(line), flush=True)
 
 
+def run_split(args):
+    """FP64 H_eff applications of the 32x32 top node (m = 128, its real product
+    counts, synthetic operators) with the FP64 contractions as exact BF16 slice
+    products on the tensor cores, beside the same applications on FP64 FMAs."""
+    import torch
+    from __graft_entry__ import build
+    from paper_2507_21236_gb300 import attn
+
+    build()
+    torch.cuda.set_device(0)
+    ctx, info = node_structure()
+    counts = info["counts"]
+    H, _ = make_heff(attn, ctx, counts)
+    stream = torch.cuda.current_stream()
+    x = torch.randn((M, M, M), device="cuda", dtype=torch.float64, generator=torch.Generator(device="cuda").manual_seed(1))
+    y = torch.empty_like(x)
+    y64 = torch.empty_like(x)
+    fl = attn.attn_heff_info(H)[2]
+    out = {}
+    for split in (1, 0):
+        cfg = attn.attn_get_config(ctx)
+        cfg.f64_split = split
+        attn.attn_set_config(ctx, cfg)
+        dst = y if split else y64
+        attn.attn_heff_apply(H, x.data_ptr(), dst.data_ptr(), attn.ATTN_F64)  # warm-up
+        attn.attn_profile_enable(ctx, True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = args.steps if split else 1
+        a.record(stream)
+        for _ in range(reps):
+            attn.attn_heff_apply(H, x.data_ptr(), dst.data_ptr(), attn.ATTN_F64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        prof = {name: attn.attn_profile_read(ctx, kid) for kid, name in ((1, "fp64_fma_gemm"), (3, "split_gemm"))}
+        attn.attn_profile_enable(ctx, False)
+        out["split" if split else "fma"] = {
+            "ms_per_apply": ms, "tflops": fl / ms / 1e9,
+            "kernels": {k: {"ms": v[0] / reps, "launches": v[1] / reps, "tflops": v[2] / max(v[0], 1e-9) / 1e9}
+                        for k, v in prof.items() if v[1]}}
+    err = float((y - y64).abs().max() / y64.abs().max())
+    print(json.dumps({"metric": "FP64 H_eff apply, 32x32 top node, m=128", "unit": "ms",
+                      "gflop_per_apply": fl / 1e9, "node_counts_pairs01_02_12_triple": list(counts[:4]),
+                      "max_rel_diff_split_vs_fma": err, "runs": out}), flush=True)
+    attn.attn_heff_destroy(H)
+    attn.attn_destroy(ctx)
+
+
 # (name, model, L, m, coupling): the matvec benchmark shapes of every configuration
 NODE_CONFIGS = [("C2", "tfim", 8, 32, 3.04), ("C3", "tfim", 16, 64, 3.04), ("C3", "tfim", 16, 128, 3.04),
                 ("C4", "heis", 16, 64, 1.0), ("C4", "heis", 16, 128, 1.0), ("C5", "tfim", 32, 128, 3.04)]
@@ -526,7 +574,7 @@ def run_nodes(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="matvec", choices=["matvec", "sweep", "nodes", "converge"])
+    ap.add_argument("--mode", default="matvec", choices=["matvec", "sweep", "nodes", "converge", "split"])
     ap.add_argument("--sweep-L", type=int, default=16)
     ap.add_argument("--sweep-m", type=int, default=32)
     ap.add_argument("--max-sweeps", type=int, default=30)
@@ -547,6 +595,8 @@ def main():
         return run_nodes(args)
     if args.mode == "converge":
         return run_converge(args)
+    if args.mode == "split":
+        return run_split(args)
     args.warmup = max(args.warmup, 3)
 
     import torch
