@@ -43,6 +43,23 @@ def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(value, world, device):
+    """The largest of every rank's value: a timed region ends when its slowest replica does."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units of all replicas per second over the (max-over-ranks) timed region."""
+    return units_per_rank * world / (ms / 1000.0)
+
+
 KERNEL_PROFILE = os.path.join(ROOT, "profiles", "sandwich_tc_kernel_tfim32x32_m128.md")
 
 
@@ -655,13 +672,8 @@ def main():
     launches = attn.attn_kernel_launches(ctx) - l0
     k_ms, k_n, k_fl = attn.attn_profile_read(ctx, 0)
     attn.attn_profile_enable(ctx, False)
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    units = iters_total * world
-    value = units / (ms / 1000.0)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, "cuda")
+    value = whole_job_rate(iters_total, world, ms)
 
     # end to end: pinned host start vector in, Ritz vector and value out, every step
     host_x = torch.empty_like(x0, device="cpu").pin_memory()
@@ -678,8 +690,8 @@ def main():
         host_y.copy_(T, non_blocking=True)
     b.record(stream)
     torch.cuda.synchronize()
-    e_ms = a.elapsed_time(b)
-    e2e = {"value": e_iters * world / (e_ms / 1000.0), "unit": "matvec/s",
+    e_ms = max_over_ranks(a.elapsed_time(b), world, "cuda")
+    e2e = {"value": whole_job_rate(e_iters, world, e_ms), "unit": "matvec/s",
            "h2d_bytes_per_step": int(x0.numel() * 8), "d2h_bytes_per_step": int(x0.numel() * 8 + 8)}
 
     peaks, src = measured_peaks()

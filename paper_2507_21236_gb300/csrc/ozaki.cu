@@ -34,7 +34,6 @@
 // of eight 16 KB stages. All waits are bounded; on a timeout the CTA records an
 // error code, stops issuing, drains its copies and frees TMEM.
 #include <algorithm>
-#include <climits>
 
 #include "ozaki.h"
 #include "tc_ptx.h"
