@@ -216,8 +216,12 @@ void gemm_f64(attn_ctx* ctx, const GemmF64& g) {
   ATTN_REQUIRE((g.M + 31) / 32 <= 65535, ATTN_EUNSUPPORTED, "GEMM M too large");
   const double fl = 2.0 * g.M * g.N * (double)g.K * g.G * g.Bhi * g.Blo;
   // marked contractions of at least ~1e8 FLOP run as exact BF16 slice products when
-  // enabled: GB300's FP64 FMA rate is a small fraction of its tensor-core rate
-  if (ctx->cfg.f64_split && g.split_ok && fl >= 1e8 && std::max(g.M, g.N) >= 32) {
+  // enabled: GB300's FP64 FMA rate is a small fraction of its tensor-core rate. The
+  // slicing grid takes at most 65535 distinct batch entries per operand.
+  const long nbA = (g.aBhi ? (long)g.Bhi : 1L) * (g.aBlo ? (long)g.Blo : 1L);
+  const long nbB = (g.bBhi ? (long)g.Bhi : 1L) * (g.bBlo ? (long)g.Blo : 1L);
+  if (ctx->cfg.f64_split && g.split_ok && fl >= 1e8 && std::max(g.M, g.N) >= 32 && nbA <= 65535 &&
+      nbB <= 65535) {
     gemm_f64_ozaki(ctx, g);
     return;
   }
