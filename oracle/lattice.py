@@ -97,7 +97,7 @@ def sum_local_terms(terms):
 
 
 def tfim_terms(lat, h):
-    """H = -sum_<ij> Z_i Z_j - h sum_i X_i (BASELINE form of Eq. qising, J = 1)."""
+    """H = -sum_<ij> Z_i Z_j - h sum_i X_i (Eq. qising with the coupling on Z, J = 1; same spectrum)."""
     terms = [((i, j), -np.kron(Z, Z)) for i, j in lat.bonds]
     terms += [((s,), -h * X) for s in range(lat.n)]
     return sum_local_terms(terms)
