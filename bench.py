@@ -272,6 +272,20 @@ def precision_arms(attn):
             "mixed_split_t12": dict(jd, f64_split=1, refine_tol=1e-12)}
 
 
+PROFILE_IDS = {0: "tc_heff_kernel", 1: "fp64_gemm", 2: "tc_gemm", 3: "split_fp64_gemm", 4: "centre_moves",
+               5: "heff_builds", 6: "lanczos", 7: "fp64_energy_refinement", 8: "de_updates"}
+
+
+def profile_report(attn, ctx, nsweeps):
+    """Stream time per sweep of the library's kernels and local-step phases (attn_profile_read)."""
+    out = {}
+    for kid, name in PROFILE_IDS.items():
+        ms, n, _ = attn.attn_profile_read(ctx, kid)
+        if n:
+            out[name] = {"ms_per_sweep": ms / max(nsweeps, 1), "count_per_sweep": n / max(nsweeps, 1)}
+    return out
+
+
 def arm_config(attn, name):
     cfg = attn.attn_config_default()
     for k, v in precision_arms(attn)[name].items():
@@ -307,6 +321,8 @@ def run_sweeps(args):
         model = attn.attn_model_tfim(ctx, Ls, h)
         st = attn.attn_state_create(ctx, model, ms, raw)
         n_de = attn.attn_de_place(st, n // 4)
+        if args.phases:
+            attn.attn_profile_enable(ctx, True)
         es, ts = [], []
         t_conv = None
         for s in range(args.max_sweeps):
@@ -320,6 +336,8 @@ def run_sweeps(args):
         out[mode] = {"energies_per_site": [e / n for e in es], "sweep_s": ts,
                      "sweeps_to_1e-8": t_conv[0] if t_conv else None,
                      "time_to_1e-8_s": t_conv[1] if t_conv else None, "n_de": n_de}
+        if args.phases:
+            out[mode]["profile"] = profile_report(attn, ctx, len(es))
         attn.attn_state_destroy(st)
         attn.attn_model_destroy(model)
         attn.attn_destroy(ctx)
@@ -385,6 +403,8 @@ def run_converge(args):
         for i, t in enumerate(tensors):
             attn.attn_node_set(st, i, t)
         es = [attn.attn_energy(st) / n]
+        if args.phases:
+            attn.attn_profile_enable(ctx, True)
         ts = []
         conv = None
         for s in range(args.max_sweeps):
@@ -397,6 +417,8 @@ def run_converge(args):
                 break
         out[name] = {"start_energy_per_site": es[0], "energies_per_site": es[1:], "sweep_s": ts,
                      "sweeps_to_1e-8": conv, "time_to_1e-8_s": sum(ts) if conv else None}
+        if args.phases:
+            out[name]["profile"] = profile_report(attn, ctx, len(ts))
         attn.attn_state_destroy(st)
         attn.attn_model_destroy(model)
         attn.attn_destroy(ctx)
@@ -603,6 +625,9 @@ def main():
                     help="converge mode: comma-separated precision arms (f64 first)")
     ap.add_argument("--sweep-arms", default="f64,mixed,mixed_k3",
                     help="sweep mode: comma-separated precision arms (f64 first)")
+    ap.add_argument("--phases", action="store_true",
+                    help="sweep/converge modes: report stream time per kernel class and local-step phase "
+                         "(event pairs around every launch: adds host overhead, keep off for timings)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)

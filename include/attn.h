@@ -117,13 +117,18 @@ ATTN_API attn_status attn_get_config(attn_ctx* ctx, attn_config* cfg);
 ATTN_API attn_status attn_sync(attn_ctx* ctx);
 /* Number of library kernels launched by this context so far. */
 ATTN_API attn_status attn_kernel_launches(attn_ctx* ctx, uint64_t* count);
-/* Kernel timing for measurement tools. enable != 0 clears the records and
- * makes the library bracket each launch of its main kernels with a CUDA event
- * pair on the context stream: kernel_id 0 = tensor-core H_eff kernel,
- * 1 = FP64 contraction kernel, 2 = tensor-core GEMM kernel. attn_profile_read
- * waits for the last recorded event and returns the summed device time (ms),
- * the number of recorded launches and their algorithmic FLOPs (Sec. 4.4.2
- * counting: 2 m_l V per operator applied on link l of a tensor of V entries). */
+/* Timing for measurement tools. enable != 0 clears the records and makes the
+ * library bracket each launch of its main kernels, and each phase of a local
+ * step, with a CUDA event pair on the context stream. kernel_id: 0 = tensor-core
+ * H_eff kernel, 1 = FP64 contraction kernel, 2 = tensor-core GEMM kernel,
+ * 3 = split FP64 GEMM (slicing and products); phases: 4 = centre moves (QR),
+ * 5 = H_eff builds (renormalisation of the node's link operators, operator
+ * stacks), 6 = Lanczos, 7 = FP64 energy and refinement, 8 = disentangler updates.
+ * attn_profile_read waits for the last recorded event and returns the summed
+ * stream time (ms, for a phase including any idle gaps between its launches),
+ * the number of recorded launches or phases and, for kernels, their algorithmic
+ * FLOPs (Sec. 4.4.2 counting: 2 m_l V per operator applied on link l of a tensor
+ * of V entries). */
 ATTN_API attn_status attn_profile_enable(attn_ctx* ctx, int enable);
 ATTN_API attn_status attn_profile_read(attn_ctx* ctx, int kernel_id, double* total_ms, int* launches, double* flops);
 

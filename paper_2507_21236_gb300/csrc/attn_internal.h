@@ -85,7 +85,7 @@ struct attn_ctx {
     double acc_ms = 0.0;          // harvested from graph replays
     double acc_flops = 0.0;
     int acc_launches = 0;
-  } prof[4];
+  } prof[9];  // ids as documented at attn_profile_enable
   // While a CUDA graph is being captured, launch events go to this list
   // (kernel id, start, stop, FLOPs) instead of the pool above.
   struct GraphEv {

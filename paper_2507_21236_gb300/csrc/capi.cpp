@@ -217,7 +217,7 @@ ATTN_API attn_status attn_profile_enable(attn_ctx* ctx, int enable) {
 ATTN_API attn_status attn_profile_read(attn_ctx* ctx, int kernel_id, double* total_ms, int* launches, double* flops) {
   ATTN_TRY
   NEED(ctx, "ctx");
-  ATTN_REQUIRE(kernel_id >= 0 && kernel_id < 4, ATTN_EINVAL, "kernel_id must be 0..3");
+  ATTN_REQUIRE(kernel_id >= 0 && kernel_id < 9, ATTN_EINVAL, "kernel_id must be 0..8");
   attn_ctx::ProfRec& p = ctx->prof[kernel_id];
   double tot = 0.0;
   if (p.used) ATTN_CHECK_CUDA(cudaEventSynchronize(p.ev[p.used - 1]));
@@ -722,7 +722,9 @@ ATTN_API attn_status attn_ttn_sweep(attn_state* st, double* energy) {
 ATTN_API attn_status attn_de_update(attn_state* st, double* dE) {
   ATTN_TRY
   NEED(st, "state");
+  st->ctx->prof_begin(8);
   double d = st->de_update(nullptr, nullptr);
+  st->ctx->prof_end(8, 0.0);
   if (dE) *dE = d;
   ATTN_CATCH
 }
@@ -739,7 +741,11 @@ ATTN_API attn_status attn_sweep(attn_state* st, double* energy) {
   ATTN_TRY
   NEED(st, "state");
   const attn_config& cfg = st->ctx->cfg;
-  if (st->sweep_count >= cfg.s_ttn && !st->des.empty()) st->de_update(nullptr, nullptr);
+  if (st->sweep_count >= cfg.s_ttn && !st->des.empty()) {
+    st->ctx->prof_begin(8);
+    st->de_update(nullptr, nullptr);
+    st->ctx->prof_end(8, 0.0);
+  }
   if (!st->mapped_ready) st->set_products();
   double e = 0;
   for (int n : st->tree.post_order()) e = st->local_step(n);

@@ -438,8 +438,12 @@ double attn_state::energy() {
 }
 
 double attn_state::local_step(int n) {
+  ctx->prof_begin(4);
   move_centre(n);
+  ctx->prof_end(4, 0.0);
+  ctx->prof_begin(5);
   attn_heff* h = build_heff(n);
+  ctx->prof_end(5, 0.0);
   const long V = vol(n);
   double result = 0.0;
   try {
@@ -456,6 +460,7 @@ double attn_state::local_step(int n) {
     // current energy (FP64): known from the last local step unless H' or a tensor changed since
     double e_cur = energy_known;
     if (!std::isfinite(e_cur)) {
+      ctx->prof_begin(7);
       lw2.wvec.reserve(sizeof(double) * V);
       ctx->scal.reserve(sizeof(double) * 64);
       double* s = ctx->scal.as<double>();
@@ -466,13 +471,18 @@ double attn_state::local_step(int n) {
       ATTN_CHECK_CUDA(cudaMemcpyAsync(hv, s, sizeof(hv), cudaMemcpyDeviceToHost, ctx->stream));
       ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
       e_cur = hv[0] / hv[1];
+      ctx->prof_end(7, 0.0);
     }
+    ctx->prof_begin(6);
     LanczosResult r = lanczos_lowest(ctx, mv_lo, v, V, cfg.lanczos_depth, cfg.lanczos_tol, lw);
+    ctx->prof_end(6, 0.0);
     double theta = r.theta;
     bool exact = (dt == ATTN_F64);
     if (dt != ATTN_F64 && cfg.refine_steps > 0) {
       // FP64 Rayleigh-Ritz with low-precision corrections: theta and v are FP64-exact for this H_eff
+      ctx->prof_begin(7);
       theta = refine_eig(ctx, mv64, mv_lo, v, V, cfg.refine_steps, cfg.refine_inner, cfg.refine_tol, rfw).theta;
+      ctx->prof_end(7, 0.0);
       exact = true;
     }
     check_device_errors(ctx, h);
