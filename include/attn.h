@@ -91,7 +91,12 @@ typedef struct {
                                environments as exact BF16 slice products on the tensor cores (Ozaki
                                scheme, 47-bit operand slices): normwise error about (K + 2) 2^-46 of the
                                operands' row scales, K the contraction length; QR stays on FP64 FMAs (0) */
-  int reserved[5];
+  int report_unconverged;   /* attn_eigsolve returns ATTN_ENOTCONVERGED (results still written) when the
+                               Lanczos residual or the refinement stopped above its tolerance (0) */
+  int wait_limit_log2;      /* consumer-side wait limit of the tensor-core H_eff kernel, 2^k clock cycles;
+                               0 = the default of about 2 s. A short limit makes the kernel give up,
+                               drain its copies and report ATTN_ETIMEOUT: for testing failure handling (0) */
+  int reserved[3];
 } attn_config;
 
 ATTN_API attn_status attn_config_default(attn_config* cfg);
@@ -252,13 +257,17 @@ ATTN_API attn_status attn_heff_apply_host(attn_heff* h, const double* x_host, do
  * (same layout as attn_heff_create), enqueued on cuda_stream (NULL: legacy
  * default stream). It calls no cudaMalloc or cudaFree; its only scratch is a
  * file-scope device array of ATTN_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB) that
- * every GPU loading the library holds until exit. Limits: m0*m1*m2 <=
+ * a GPU holds, once committed, until the process exits. Limits: m0*m1*m2 <=
  * ATTN_NOALLOC_SCRATCH_DOUBLES, or half of it when n_triple > 0; larger sizes
  * return ATTN_EINVAL with a message. The first call on each device looks up
- * the scratch array's device address (with that device current), so make
- * that first call before any stream capture. Every call shares the one
- * array: calls whose work overlaps on the GPU (other streams, other threads
- * on the same device) race and must be serialised by the caller. */
+ * the scratch array's device address (with that device current). CUDA loads a
+ * library's device code lazily by default, so that first call is also when the
+ * 16 MiB are committed on the device: make it before the framework reserves
+ * its memory pool (or run with CUDA_MODULE_LOADING=EAGER, which commits the
+ * array when the library is loaded), and before any stream capture. Every
+ * call shares the one array, which keeps the last call's contents: calls
+ * whose work overlaps on the GPU (other streams, other threads on the same
+ * device) race and must be serialised by the caller. */
 #define ATTN_NOALLOC_SCRATCH_DOUBLES (1L << 21)
 ATTN_API attn_status attn_heff_apply_f64_static(const attn_heff_desc* desc, const double* x_dev, double* y_dev,
                                                 void* cuda_stream);

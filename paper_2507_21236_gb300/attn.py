@@ -31,7 +31,8 @@ class attn_config(ctypes.Structure):
                 ("s_ttn", ctypes.c_int), ("matvec_dtype", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("refine_tol", ctypes.c_double),
                 ("use_graphs", ctypes.c_int), ("refine_inner", ctypes.c_int),
-                ("f64_split", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("f64_split", ctypes.c_int), ("report_unconverged", ctypes.c_int),
+                ("wait_limit_log2", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class attn_heff_desc(ctypes.Structure):

@@ -38,10 +38,13 @@ struct Error {
   } while (0)
 
 // ------------------------------------------------------------ device memory
-// Owning device buffer (cudaMalloc / cudaFree).
+// Owning device buffer (cudaMalloc / cudaFree). A buffer that captured CUDA graphs
+// may reference carries an epoch counter, bumped whenever the buffer is
+// reallocated, so that graphs built on the old address can be detected.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  uint64_t* epoch = nullptr;  // not owned; bumped on every reallocation
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
@@ -67,7 +70,10 @@ struct attn_ctx {
   uint64_t launches = 0;
   int device = 0;
   int num_sms = 0;
-  // Scratch areas reused across calls (grow only).
+  // Scratch areas reused across calls (grow only). Every reallocation of one of
+  // them bumps scratch_epoch: a captured eigensolve graph records the epoch it was
+  // built under and is rebuilt when it differs (its kernels hold the old addresses).
+  uint64_t scratch_epoch = 0;
   attn::DevBuf ws[4];
   attn::DevBuf scal;      // small device scalars
   attn::DevBuf partials;  // reduction partials (fixed size, allocated at creation)

@@ -34,6 +34,7 @@ void DevBuf::release() {
 void DevBuf::reserve(size_t n) {
   if (n <= bytes && p) return;
   release();
+  if (epoch) ++*epoch;
   size_t want = std::max<size_t>(n, 256);
   cudaError_t e = cudaMalloc(&p, want);
   if (e != cudaSuccess) {
@@ -158,6 +159,9 @@ ATTN_API attn_status attn_create(const attn_config* cfg, void* stream, attn_ctx*
   // NULL selects the legacy default stream (what torch's default stream reports as 0)
   ctx->stream = stream ? (cudaStream_t)stream : (cudaStream_t)0;
   ctx->own_stream = false;
+  for (DevBuf* b : {&ctx->ws[0], &ctx->ws[1], &ctx->ws[2], &ctx->ws[3], &ctx->scal, &ctx->partials,
+                    &ctx->gsplit_ws, &ctx->oz_ws[0], &ctx->oz_ws[1], &ctx->oz_ws[2], &ctx->oz_ws[3], &ctx->oz_err})
+    b->epoch = &ctx->scratch_epoch;
   ctx->partials.reserve(sizeof(double) * 512 * 64);
   ctx->scal.reserve(sizeof(double) * 64);
   *out = ctx.release();
@@ -180,6 +184,7 @@ ATTN_API attn_status attn_set_config(attn_ctx* ctx, const attn_config* cfg) {
   ATTN_REQUIRE(cfg->lanczos_depth >= 1 && cfg->lanczos_depth <= 60, ATTN_EINVAL, "lanczos_depth must be 1..60");
   ATTN_REQUIRE(cfg->matvec_dtype == ATTN_F64 || cfg->matvec_dtype == ATTN_BF16, ATTN_EUNSUPPORTED,
                "matvec_dtype must be ATTN_F64 or ATTN_BF16");
+  ATTN_REQUIRE(cfg->wait_limit_log2 >= 0 && cfg->wait_limit_log2 <= 62, ATTN_EINVAL, "wait_limit_log2 must be 0..62");
   ctx->cfg = *cfg;
   ATTN_CATCH
 }
@@ -614,8 +619,12 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
   const int rsteps = (dt != ATTN_F64) ? cfg.refine_steps : 0;
   if (cfg.use_graphs) {
     EigGraph* g = h->eg;
+    // a graph holds the addresses of the context's scratch buffers at capture time:
+    // any reallocation since (scratch_epoch) or a change of the FP64 contraction path
+    // (f64_split) makes it stale
     if (!g || g->x != T_dev || g->depth != cfg.lanczos_depth || g->tol != cfg.lanczos_tol || g->dtype != dt ||
-        g->refine != rsteps || g->rtol != cfg.refine_tol || g->prof != ctx->prof_on) {
+        g->refine != rsteps || g->rtol != cfg.refine_tol || g->prof != ctx->prof_on ||
+        g->f64_split != cfg.f64_split || g->epoch != ctx->scratch_epoch) {
       delete g;
       g = h->eg = new EigGraph();
       g->x = T_dev;
@@ -625,6 +634,7 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
       g->refine = rsteps;
       g->rtol = cfg.refine_tol;
       g->prof = ctx->prof_on;
+      g->f64_split = cfg.f64_split;
       // warm-up on a scratch copy: every buffer the solve needs is allocated before capture
       ctx->ws[3].reserve(sizeof(double) * h->V);
       copy_f64(ctx, ctx->ws[3].as<double>(), T_dev, h->V);
@@ -633,6 +643,7 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
       lanczos_enqueue(ctx, lo, ctx->ws[3].as<double>(), h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0);
       ctx->prof_on = prof_was;
       ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+      g->epoch_before = ctx->scratch_epoch;
       cudaStream_t user = ctx->stream, cs;
       ATTN_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
       const uint64_t l0 = ctx->launches;
@@ -659,11 +670,16 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
       ATTN_CHECK_CUDA(cudaStreamDestroy(cs));
       g->launches = ctx->launches - l0;
       ctx->launches = l0;
+      // the warm-up sized every scratch buffer, so none may have moved during the capture
+      ATTN_REQUIRE(ctx->scratch_epoch == g->epoch_before, ATTN_ECUDA,
+                   "a scratch buffer was reallocated while the eigensolve graph was captured");
+      g->epoch = ctx->scratch_epoch;
       ATTN_CHECK_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
     }
     ATTN_CHECK_CUDA(cudaGraphLaunch(g->exec, ctx->stream));
     ctx->launches += g->launches;
-    LanczosResult r = lanczos_read(ctx, g->w);
+    LanczosResult r = timeout_first(ctx, h, [&] { return lanczos_read(ctx, g->w); });
+    r.converged = r.resid < cfg.lanczos_tol * std::max(std::fabs(r.theta), 1e-300);
     for (auto& e : g->evs) {
       float ms = 0.f;
       ATTN_CHECK_CUDA(cudaEventElapsedTime(&ms, e.a, e.b));
@@ -673,29 +689,43 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
     }
     *theta = r.theta;
     int it = r.iters;
+    bool conv = r.converged;
     if (rsteps > 0) {
-      RefineResult f = refine_eig(ctx, hi, lo, T_dev, h->V, rsteps, cfg.refine_inner, cfg.refine_tol, g->rw);
+      RefineResult f = timeout_first(ctx, h, [&] {
+        return refine_eig(ctx, hi, lo, T_dev, h->V, rsteps, cfg.refine_inner, cfg.refine_tol, g->rw);
+      });
       *theta = f.theta;
       it += f.fp64_matvecs + f.lo_matvecs;
+      conv = f.converged;
     }
     check_device_errors(ctx, h);
     if (iters) *iters = it;
+    ATTN_REQUIRE(!(cfg.report_unconverged && !conv), ATTN_ENOTCONVERGED,
+                 "the eigensolve stopped above its tolerance (best Ritz pair written)");
     return ATTN_OK;
   }
   LanczosWork w;
-  LanczosResult r = lanczos_lowest(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, w);
+  LanczosResult r = timeout_first(ctx, h, [&] {
+    return lanczos_lowest(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, w);
+  });
   double th = r.theta;
   int it = r.iters;
+  bool conv = r.converged;
   if (rsteps > 0) {
     RefineWork rw;
-    RefineResult f = refine_eig(ctx, hi, lo, T_dev, h->V, rsteps, cfg.refine_inner, cfg.refine_tol, rw);
+    RefineResult f = timeout_first(ctx, h, [&] {
+      return refine_eig(ctx, hi, lo, T_dev, h->V, rsteps, cfg.refine_inner, cfg.refine_tol, rw);
+    });
     th = f.theta;
     it += f.fp64_matvecs + f.lo_matvecs;
+    conv = f.converged;
   }
   ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
   check_device_errors(ctx, h);
   *theta = th;
   if (iters) *iters = it;
+  ATTN_REQUIRE(!(cfg.report_unconverged && !conv), ATTN_ENOTCONVERGED,
+               "the eigensolve stopped above its tolerance (best Ritz pair written)");
   ATTN_CATCH
 }
 

@@ -10,9 +10,11 @@ struct EigGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   const double* x = nullptr;
-  int depth = 0, dtype = 0, refine = 0;
+  int depth = 0, dtype = 0, refine = 0, f64_split = 0;
   double tol = 0.0, rtol = 0.0;
   bool prof = false;
+  uint64_t epoch = ~0ull;         // the context's scratch_epoch the graph was captured under
+  uint64_t epoch_before = ~0ull;  // the same, read before the capture began
   uint64_t launches = 0;
   attn::LanczosWork w;
   attn::RefineWork rw;
@@ -59,6 +61,18 @@ int tc_error(attn_heff* h);
 // Throws ATTN_ETIMEOUT when a bounded wait in a tensor-core kernel gave up (the
 // H_eff's tensor-core error word, if h is given, and the split FP64 GEMM's).
 void check_device_errors(attn_ctx* ctx, attn_heff* h);
+// Runs f(); if it throws, a device-side timeout recorded meanwhile is reported in
+// its place (a kernel that gave up leaves its outputs unwritten, which the host
+// may then see as non-finite values).
+template <class F>
+auto timeout_first(attn_ctx* ctx, attn_heff* h, F&& f) -> decltype(f()) {
+  try {
+    return f();
+  } catch (const Error&) {
+    check_device_errors(ctx, h);
+    throw;
+  }
+}
 // y += sum_{r<R} A_r x_p W_r with W_r per-product tensors (stride V), FP64.
 void accumulate_slot_f64(attn_ctx* ctx, const int d[3], int p, const double* A, int R, const double* W, double* y);
 }  // namespace attn

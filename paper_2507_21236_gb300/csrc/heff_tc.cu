@@ -90,6 +90,7 @@ struct TcParams {
   KindParams kind[3];
   int nkinds;
   int* err;           // device error word (0 = ok)
+  long long wait;     // wait limit (cycles) of the MMA-issue, conversion and epilogue threads
 };
 
 struct TcMaps {
@@ -243,12 +244,12 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     const int nkbX = kPP ? nsl * nkbQ : 0;  // ring K blocks of X per product
     if (warp == 1) {
       const uint64_t dX0 = sw128_desc(sX);  // X block kb of slice u: + (32 KB kb + 16 KB u) >> 4
-      bool ok = kPP ? true : mbar_wait(bar(XFULL), 0, prm.err, 31, abort_flag);
+      bool ok = kPP ? true : mbar_wait(bar(XFULL), 0, prm.err, 31, abort_flag, prm.wait);
       for (int r = 0; ok && r < R; ++r) {
         // stage 1 per slice: D1_u = B_r X_u^T (the B_r blocks serve both slices)
         for (int u = 0; ok && u < nsl; ++u) {
           // D1_u holds Z_u of product r-1 until its stage 2 has completed
-          if (r > 0 && !mbar_wait(bar(S2DONE + u), (r - 1) & 1, prm.err, 35, abort_flag)) { ok = false; break; }
+          if (r > 0 && !mbar_wait(bar(S2DONE + u), (r - 1) & 1, prm.err, 35, abort_flag, prm.wait)) { ok = false; break; }
           fence_after();
           int s1 = st;
           uint32_t p1 = ph;
@@ -256,8 +257,8 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
           uint32_t px = ph;
           while (sx >= NS) { sx -= NS; px ^= 1u; }
           for (int kb = 0; kb < nkbQ; ++kb) {
-            if (u == 0 && !mbar_wait(barFull + 8 * s1, p1, prm.err, 32, abort_flag)) { ok = false; break; }
-            if (kPP && !mbar_wait(barFull + 8 * sx, px, prm.err, 36, abort_flag)) { ok = false; break; }
+            if (u == 0 && !mbar_wait(barFull + 8 * s1, p1, prm.err, 32, abort_flag, prm.wait)) { ok = false; break; }
+            if (kPP && !mbar_wait(barFull + 8 * sx, px, prm.err, 36, abort_flag, prm.wait)) { ok = false; break; }
             const uint64_t dB = dRing0 + (uint64_t)(s1 * (kKBlockBytes >> 4));
             const uint64_t dX = kPP ? dRing0 + (uint64_t)(sx * (kKBlockBytes >> 4))
                                     : dX0 + (uint64_t)((kb * kTileBytes + u * (kTileBytes / 2)) >> 4);
@@ -290,8 +291,8 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
           int s2 = st;
           uint32_t p2 = ph;
           for (int kb = 0; kb < nkbP; ++kb) {
-            if (!mbar_wait(bar(ZFULL + 2 * u + kb), r & 1, prm.err, 34, abort_flag)) { ok = false; break; }
-            if (u == 0 && !mbar_wait(barFull + 8 * s2, p2, prm.err, 33, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(bar(ZFULL + 2 * u + kb), r & 1, prm.err, 34, abort_flag, prm.wait)) { ok = false; break; }
+            if (u == 0 && !mbar_wait(barFull + 8 * s2, p2, prm.err, 33, abort_flag, prm.wait)) { ok = false; break; }
             fence_after();  // Z was written by tcgen05.st in other threads
             const uint64_t dA = dRing0 + (uint64_t)(s2 * (kKBlockBytes >> 4));
             const uint32_t aZ = tD1(u) + 64u * (uint32_t)kb;
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     bool ok = u < nsl && c0 < P;
     for (int r = 0; ok && r < R; ++r) {
       // warp-uniform: the TMEM accesses below are .sync.aligned
-      if (!__all_sync(0xffffffffu, mbar_wait(bar(D1FULL + u), r & 1, prm.err, 41, abort_flag))) { ok = false; break; }
+      if (!__all_sync(0xffffffffu, mbar_wait(bar(D1FULL + u), r & 1, prm.err, 41, abort_flag, prm.wait))) { ok = false; break; }
       fence_after();
       uint32_t w[32];  // packed BF16 pairs of this thread's 64 columns
 #pragma unroll
@@ -345,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(ZFULL + 2 * u + hh));
     }
-    if (ok && R > 0 && __all_sync(0xffffffffu, mbar_wait(bar(D2FULL), 0, prm.err, 43, abort_flag))) {
+    if (ok && R > 0 && __all_sync(0xffffffffu, mbar_wait(bar(D2FULL), 0, prm.err, 43, abort_flag, prm.wait))) {
       fence_after();
       float* yp = kp.Y + ((long)(s0 + u) * P + c0) * Q + j;  // walks down column j of Y_s
       // partial sums of a split product list meet here, and per-product results add onto the pair result
@@ -629,6 +630,9 @@ void attn_heff::apply_bf16(const double* x, double* y) {
   if (!tc_ready) tc_build(this);
   TcState* t = static_cast<TcState*>(tc);
   cudaStream_t st = ctx->stream;
+  // consumer-side wait limit (a short one is how tests make the kernel give up)
+  const int wl = ctx->cfg.wait_limit_log2;
+  t->prm.wait = t->tprm.wait = (wl > 0) ? (1LL << std::min(wl, 62)) : attn::tc::kWaitCycles;
   // the kind buffers are indexed by pair kind k (0,1,2); kinds with no products pass null
   prep_x_kernel<<<tile_grid(m), dim3(kTile, 8), 0, st>>>(x, m[0], m[1], m[2], t->R[0] ? t->x[0].as<__nv_bfloat16>() : nullptr,
                                           t->R[1] ? t->x[1].as<__nv_bfloat16>() : nullptr,

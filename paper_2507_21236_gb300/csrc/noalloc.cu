@@ -8,7 +8,8 @@
 // y = H_eff x as attn_heff_create + attn_heff_apply(ATTN_F64) but reads the
 // caller's operator arrays in place and uses, as its only scratch, one
 // file-scope device array of ATTN_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB),
-// which every GPU that loads the library holds until the process exits.
+// which a GPU holds, once committed by the first call there, until the process
+// exits (CUDA loads device code lazily by default).
 #include <mutex>
 
 #include "attn_internal.h"

@@ -474,14 +474,17 @@ double attn_state::local_step(int n) {
       ctx->prof_end(7, 0.0);
     }
     ctx->prof_begin(6);
-    LanczosResult r = lanczos_lowest(ctx, mv_lo, v, V, cfg.lanczos_depth, cfg.lanczos_tol, lw);
+    LanczosResult r =
+        timeout_first(ctx, h, [&] { return lanczos_lowest(ctx, mv_lo, v, V, cfg.lanczos_depth, cfg.lanczos_tol, lw); });
     ctx->prof_end(6, 0.0);
     double theta = r.theta;
     bool exact = (dt == ATTN_F64);
     if (dt != ATTN_F64 && cfg.refine_steps > 0) {
       // FP64 Rayleigh-Ritz with low-precision corrections: theta and v are FP64-exact for this H_eff
       ctx->prof_begin(7);
-      theta = refine_eig(ctx, mv64, mv_lo, v, V, cfg.refine_steps, cfg.refine_inner, cfg.refine_tol, rfw).theta;
+      theta = timeout_first(ctx, h, [&] {
+                return refine_eig(ctx, mv64, mv_lo, v, V, cfg.refine_steps, cfg.refine_inner, cfg.refine_tol, rfw);
+              }).theta;
       ctx->prof_end(7, 0.0);
       exact = true;
     }

@@ -37,13 +37,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false (and `code` recorded in *err) after ~kWaitCycles or once another thread aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, volatile int* abort_flag) {
+// Bounded wait: false (and `code` recorded in *err) after `limit` cycles (~kWaitCycles by
+// default) or once another thread aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, volatile int* abort_flag,
+                                          long long limit = kWaitCycles) {
   if (mbar_try_wait(bar, parity)) return true;  // fast path: no clock read when already complete
   long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicCAS(err, 0, code);
       *abort_flag = 1;
       return false;

@@ -99,3 +99,37 @@ def test_graph_eigsolve_equals_plain():
     attn.attn_state_destroy(st)
     attn.attn_model_destroy(mod)
     attn.attn_destroy(ctx)
+
+
+def test_graph_cache_rebuilt_after_scratch_reallocation():
+    """Two explicit H_eff of different sizes take turns in graph-replayed FP64
+    eigensolves on one context. The larger one grows the context's shared matvec
+    scratch, so the smaller one's cached graph holds a stale address and must be
+    rebuilt; every solve must equal the plain (non-graph) solve of the same H_eff."""
+    import torch
+    from inputs import random_operators, random_vector
+
+    def heff(attn, ctx, shape, npair, seed):
+        h = [dev(random_operators(1, shape[s], seed, 10 + s)[0]) for s in range(3)]
+        pairs = {k: (dev(random_operators(npair, shape[(0, 0, 1)[k]], seed, 20 + k)),
+                     dev(random_operators(npair, shape[(1, 2, 2)[k]], seed, 30 + k))) for k in range(3)}
+        return attn.attn_heff_create(ctx, shape, h, pairs, None), (h, pairs)
+
+    results = {}
+    for g in (0, 1):
+        attn, ctx = lib_and_ctx({"use_graphs": g, "matvec_dtype": 0, "lanczos_tol": 0.0, "lanczos_depth": 12})
+        Hs, keep = zip(*[heff(attn, ctx, (8, 8, 8), 6, 1), heff(attn, ctx, (32, 32, 16), 40, 2)])
+        x0 = [random_vector((8, 8, 8), 3), random_vector((32, 32, 16), 4)]
+        bufs = [dev(x) for x in x0]
+        out = []
+        for i in (0, 1, 0, 1, 0):
+            bufs[i].copy_(torch.as_tensor(x0[i], device="cuda"))
+            th, _ = attn.attn_eigsolve(Hs[i], bufs[i])
+            out.append((th, host(bufs[i]).copy()))
+        results[g] = out
+        for H in Hs:
+            attn.attn_heff_destroy(H)
+        attn.attn_destroy(ctx)
+    for (t0, v0), (t1, v1) in zip(results[0], results[1]):
+        assert abs(t0 - t1) <= 1e-13 * abs(t0)
+        assert np.abs(v0 - v1).max() <= 1e-12
