@@ -199,18 +199,49 @@ def make_heff(attn, ctx, counts, seed=0):
     return H, (h_int, pairs, trip)
 
 
-def cpu_baseline(counts, budget_s=15.0):
-    """FP64 oracle H_eff on the host cores: time per product on a sample, scaled."""
+def oracle_node_structure():
+    """Product counts of the top node from the oracle's own placement, mapping and
+    rank-1 split (no library code): pairs (0,1), (0,2), (1,2), triple, internal."""
+    from inputs import normal
+    from oracle.disentangle import map_terms, place_disentanglers, products_of
+    from oracle.lattice import square_lattice, tfim_terms
+    from oracle.tree import Tree
+
+    terms = tfim_terms(square_lattice(L), H_FIELD)
+    tree = Tree(L * L, 16)  # the placement rule gives the same pairs for every m in [16, 255]
+    des = place_disentanglers(tree, terms, N_DE)
+    us = []
+    for k in range(len(des)):
+        q, r = np.linalg.qr(normal(11, 5000 + k, 16).reshape(4, 4))
+        us.append(q * np.sign(np.diag(r)))
+    top = tree.top_nodes()[0]
+    regions = [set(tree.region(top, s)) for s in range(3)]
+    counts = [0] * 5
+    slot_of_mask = {3: 0, 5: 1, 6: 2, 7: 3}
+    for sites, _, _ in products_of(map_terms(terms, des, us)):
+        mask = 0
+        for x in sites:
+            for k in range(3):
+                if x in regions[k]:
+                    mask |= 1 << k
+        counts[slot_of_mask.get(mask, 4)] += 1
+    return counts
+
+
+def oracle_sample(budget_s, counts):
+    """FP64 oracle H_eff on this process's host threads: the median time of single
+    pair products of the [128]^3 top node (random operators; the cost does not depend
+    on their values), scaled to the node's product list."""
     from inputs import random_operators, random_vector
     from oracle.ttn import heff_apply_ops
 
     x = random_vector((M, M, M), 1)
     total = counts[0] + counts[1] + counts[2]
-    t0 = time.perf_counter()
-    done = 0
     kinds = [(0, 1), (0, 2), (1, 2)]
     per_kind = {}
-    while time.perf_counter() - t0 < budget_s and done < total:
+    t0 = time.perf_counter()
+    done = 0
+    while (time.perf_counter() - t0 < budget_s or done < 3) and done < total:
         k = done % 3
         a = random_operators(1, M, 7, 100 + done)
         b = random_operators(1, M, 7, 200 + done)
@@ -218,46 +249,124 @@ def cpu_baseline(counts, budget_s=15.0):
         heff_apply_ops(x, (None, None, None), {kinds[k]: (a, b)})
         per_kind.setdefault(k, []).append(time.perf_counter() - t1)
         done += 1
-    t_prod = {k: statistics.median(v) for k, v in per_kind.items()}
-    est = sum(counts[k] * t_prod.get(k, statistics.median(sum(per_kind.values(), []))) for k in range(3))
-    est += counts[3] * 1.5 * statistics.median(sum(per_kind.values(), []))  # three-link products
-    cores = os.cpu_count()
-    try:
-        import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        cores = max(i.get("num_threads", 1) for i in info) if info else cores
-    except Exception:
-        pass
-    return {"value": 1.0 / est, "unit": "matvec/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} of {total} pair products of the [128]^3 top-node H_eff applied by the FP64 "
-                      f"oracle (numpy), median time per product scaled to the full term list"}
+    med_all = statistics.median(sum(per_kind.values(), []))
+    est = sum(counts[k] * statistics.median(per_kind.get(k, [med_all])) for k in range(3))
+    est += counts[3] * 1.5 * med_all  # a three-link product: three mode products instead of two
+    return {"value": 1.0 / est, "products_timed": done, "products_total": total}
+
+
+def cpu_baseline(counts, budget_s=15.0):
+    """The oracle timed on the host cores, single-threaded and with every core (the BLAS
+    thread count is fixed in a child process before numpy loads)."""
+    out = {}
+    for threads in (1, os.cpu_count() or 1):
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+                   MKL_NUM_THREADS=str(threads))
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--mode", "oracle_sample",
+                            "--sample-s", str(budget_s), "--counts", ",".join(map(str, counts))],
+                           env=env, capture_output=True, text=True, check=True)
+        out[threads] = json.loads(r.stdout.strip().splitlines()[-1])
+    cores = max(out)
+    return {"value": out[cores]["value"], "unit": "matvec/s", "cores": cores, "kind": "oracle",
+            "single_thread_value": out[1]["value"],
+            "sample": f"{out[cores]['products_timed']} of {out[cores]['products_total']} pair products of the "
+                      f"[128]^3 top-node H_eff applied one by one by the FP64 oracle (numpy) in about "
+                      f"{budget_s:.0f} s per thread count; the median time per product scaled to the node's "
+                      f"full product list (counts from the oracle's own placement and mapping)"}
 
 
 def run_reference(args):
     rank, world, _ = rank_info()
     if rank != 0:
         return
-    counts = (288, 288, 288, 0)
-    try:
-        import torch  # noqa: F401
-        _, info = node_structure()
-        counts = info["counts"]
-    except Exception:
-        pass
+    counts = oracle_node_structure()
+    budget = max(2.0, 20.0 / max(args.steps + args.warmup, 1))
     vals = []
     for _ in range(args.warmup + args.steps):
-        vals.append(cpu_baseline(counts, budget_s=max(2.0, 20.0 / max(args.steps, 1)))["value"])
+        vals.append(oracle_sample(budget, counts)["value"])
     vals = vals[args.warmup:]
     v = statistics.median(vals)
-    cb = cpu_baseline(counts, budget_s=2.0)
+    cores = os.cpu_count() or 1
     line = {"impl": "reference", "metric": "H_eff matvecs/s at m=128", "value": v, "unit": "matvec/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "model": "tfim", "L": L, "m": M},
-            "cpu_baseline": {"value": v, "unit": "matvec/s", "cores": cb["cores"], "kind": "oracle",
-                             "sample": cb["sample"]},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "model": "tfim", "L": L, "m": M,
+                                            "node_counts_pairs01_02_12_triple_internal": counts},
+            "cpu_baseline": {"value": v, "unit": "matvec/s", "cores": cores, "kind": "oracle",
+                             "sample": f"per step: about {budget:.1f} s of single pair products of the [128]^3 "
+                                       f"top-node H_eff applied by the FP64 oracle (numpy, default BLAS threads), "
+                                       f"median time per product scaled to the oracle's own product list"},
             "e2e": {"value": v, "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def mixed_solve_record(attn, ctx, H, x0, torch):
+    """One accuracy-bearing mixed solve of the timed node against the FP64 solve."""
+    stream = torch.cuda.current_stream()
+    base = attn.attn_get_config(ctx)
+    out = {}
+    for name, upd in (("f64_split", {"matvec_dtype": attn.ATTN_F64, "f64_split": 1, "refine_steps": 0}),
+                      ("mixed_split", {"matvec_dtype": attn.ATTN_BF16, "f64_split": 1, "refine_steps": 3,
+                                       "refine_inner": 16, "refine_tol": 1e-10})):
+        cfg = attn.attn_get_config(ctx)
+        for k, v in upd.items():
+            setattr(cfg, k, v)
+        cfg.use_graphs = 0
+        cfg.lanczos_tol = 1e-13
+        attn.attn_set_config(ctx, cfg)
+        T = x0.clone()
+        attn.attn_eigsolve(H, T.data_ptr())  # warm-up (tensor-core tuning, split workspaces)
+        T = x0.clone()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        theta, iters = attn.attn_eigsolve(H, T.data_ptr())
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms": a.elapsed_time(b), "theta": theta, "matvecs": iters}
+    attn.attn_set_config(ctx, base)
+    ref = out["f64_split"]["theta"]
+    out["theta_rel_diff"] = abs(out["mixed_split"]["theta"] - ref) / abs(ref)
+    out["note"] = ("depth-20 Lanczos from the same start: FP64 (split) matvecs vs BF16 matvecs + 3 FP64 "
+                   "Rayleigh-Ritz refinements with BF16 Jacobi-Davidson inner solves")
+    return out
+
+
+SWEEP_L, SWEEP_M, SWEEP_N = 16, 128, 2
+
+
+def sweep_record(attn, torch):
+    """16x16 TFIM (h = 3.04), m = 128: the first two aTTN sweeps (S_TTN = 1, then
+    disentangler updates) of the FP64 path (contractions as split BF16 products) and
+    of the mixed path (BF16 Lanczos + FP64 refinement), from the same tensors."""
+    from inputs import raw_tree_tensors
+
+    n = SWEEP_L * SWEEP_L
+    raw = raw_tree_tensors(tree_shapes(n, SWEEP_M), 0)
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for name in ("f64_split", "mixed_split"):
+        cfg = arm_config(attn, name)
+        ctx = attn.attn_create(cfg, stream)
+        model = attn.attn_model_tfim(ctx, SWEEP_L, H_FIELD)
+        st = attn.attn_state_create(ctx, model, SWEEP_M, raw)
+        n_de = attn.attn_de_place(st, n // 4)
+        es, ts = [], []
+        for _ in range(SWEEP_N):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            es.append(attn.attn_sweep(st) / n)
+            ts.append(time.perf_counter() - t0)
+        out[name] = {"s_per_sweep": ts, "energy_per_site": es, "n_de": n_de}
+        attn.attn_state_destroy(st)
+        attn.attn_model_destroy(model)
+        attn.attn_destroy(ctx)
+    out["mixed_minus_f64_per_site"] = [a - b for a, b in zip(out["mixed_split"]["energy_per_site"],
+                                                               out["f64_split"]["energy_per_site"])]
+    out["config"] = {"workload": f"tfim{SWEEP_L}x{SWEEP_L}_m{SWEEP_M}_first_{SWEEP_N}_sweeps", "s_ttn": 1,
+                     "mixed": "bf16 Lanczos + <= 8 FP64 Rayleigh-Ritz corrections from 16-step bf16 CG "
+                              "Jacobi-Davidson solves until theta moves by < 1e-10 |theta|; FP64 contractions "
+                              "as split bf16 products (f64_split) in both arms"}
+    return out
 
 
 def precision_arms(attn):
@@ -490,6 +599,45 @@ def run_split(args):
     attn.attn_destroy(ctx)
 
 
+def run_sttn(args):
+    """The S_TTN study of Sec. 6.3 (Fig. benchmark-4deopt) at a size one GPU call affords:
+    the same total number of sweeps, of which the first S_TTN run without disentangler
+    optimisation and the rest update the disentangler layer every sweep; final energy
+    per site and run time for each S_TTN."""
+    import torch
+    from __graft_entry__ import build
+    from inputs import raw_tree_tensors
+    from paper_2507_21236_gb300 import attn
+
+    build()
+    Ls, ms = args.sweep_L, args.sweep_m
+    n = Ls * Ls
+    raw = raw_tree_tensors(tree_shapes(n, ms), 0)
+    stream = torch.cuda.current_stream().cuda_stream
+    rows = []
+    for s_ttn in [int(v) for v in args.sttn_values.split(",")]:
+        cfg = arm_config(attn, args.sttn_arm)
+        cfg.s_ttn = s_ttn
+        ctx = attn.attn_create(cfg, stream)
+        model = attn.attn_model_tfim(ctx, Ls, H_FIELD)
+        st = attn.attn_state_create(ctx, model, ms, raw)
+        n_de = attn.attn_de_place(st, n // 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        es = [attn.attn_sweep(st) / n for _ in range(args.max_sweeps)]
+        rows.append({"s_ttn": s_ttn, "energy_per_site": es, "final": es[-1], "s": time.perf_counter() - t0,
+                     "n_de": n_de})
+        print(json.dumps(rows[-1]), flush=True)
+        attn.attn_state_destroy(st)
+        attn.attn_model_destroy(model)
+        attn.attn_destroy(ctx)
+    best = min(rows, key=lambda r: r["final"])
+    print(json.dumps({"metric": "final energy per site vs S_TTN (fixed total sweeps)", "unit": "E/site",
+                      "best_s_ttn": best["s_ttn"], "config": {"workload": f"tfim{Ls}x{Ls}_m{ms}_sttn", "L": Ls,
+                      "m": ms, "h": H_FIELD, "sweeps": args.max_sweeps, "arm": args.sttn_arm}, "runs": rows}),
+          flush=True)
+
+
 # (name, model, L, m, coupling): the matvec benchmark shapes of every configuration
 NODE_CONFIGS = [("C2", "tfim", 8, 32, 3.04), ("C3", "tfim", 16, 64, 3.04), ("C3", "tfim", 16, 128, 3.04),
                 ("C4", "heis", 16, 64, 1.0), ("C4", "heis", 16, 128, 1.0), ("C5", "tfim", 32, 128, 3.04)]
@@ -616,7 +764,8 @@ def run_nodes(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="matvec", choices=["matvec", "sweep", "nodes", "converge", "split"])
+    ap.add_argument("--mode", default="matvec",
+                    choices=["matvec", "sweep", "nodes", "converge", "split", "sttn", "oracle_sample"])
     ap.add_argument("--sweep-L", type=int, default=16)
     ap.add_argument("--sweep-m", type=int, default=32)
     ap.add_argument("--max-sweeps", type=int, default=30)
@@ -625,6 +774,8 @@ def main():
                     help="converge mode: comma-separated precision arms (f64 first)")
     ap.add_argument("--sweep-arms", default="f64,mixed,mixed_k3",
                     help="sweep mode: comma-separated precision arms (f64 first)")
+    ap.add_argument("--sttn-values", default="0,1,2,3,5", help="sttn mode: S_TTN values to compare")
+    ap.add_argument("--sttn-arm", default="mixed_split", help="sttn mode: precision arm of every run")
     ap.add_argument("--phases", action="store_true",
                     help="sweep/converge modes: report stream time per kernel class and local-step phase "
                          "(event pairs around every launch: adds host overhead, keep off for timings)")
@@ -633,7 +784,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="attn")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="matvec mode: skip the 16x16 m=128 sweep record")
+    ap.add_argument("--sample-s", type=float, default=15.0, help=argparse.SUPPRESS)
+    ap.add_argument("--counts", default="", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.mode == "oracle_sample":
+        print(json.dumps(oracle_sample(args.sample_s, [int(c) for c in args.counts.split(",")])), flush=True)
+        return
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "sweep":
@@ -644,6 +801,8 @@ def main():
         return run_converge(args)
     if args.mode == "split":
         return run_split(args)
+    if args.mode == "sttn":
+        return run_sttn(args)
     args.warmup = max(args.warmup, 3)
 
     import torch
@@ -705,31 +864,36 @@ def main():
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), world, "cuda")
     value = whole_job_rate(iters_total, world, ms)
 
-    # end to end: pinned host start vector in, Ritz vector and value out, every step
-    host_x = torch.empty_like(x0, device="cpu").pin_memory()
-    host_x.copy_(x0.cpu())
-    host_y = torch.empty_like(host_x).pin_memory()
+    # end to end through the C ABI on host buffers: every step one attn_eigsolve_host
+    # call copies the start tensor in, solves and copies the Ritz vector back
+    host_T = torch.empty(x0.shape, dtype=torch.float64).pin_memory()
+    host_np = host_T.numpy()
+    x0_host = x0.cpu().numpy()
     torch.cuda.synchronize()
     e_iters = 0
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        T.copy_(host_x, non_blocking=True)
-        theta, it = attn.attn_eigsolve(H, T.data_ptr())
+        host_np[...] = x0_host
+        theta, it = attn.attn_eigsolve_host(H, host_np)
         e_iters += it
-        host_y.copy_(T, non_blocking=True)
-    b.record(stream)
-    torch.cuda.synchronize()
-    e_ms = max_over_ranks(a.elapsed_time(b), world, "cuda")
+    e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0, world, "cuda")
     e2e = {"value": whole_job_rate(e_iters, world, e_ms), "unit": "matvec/s",
-           "h2d_bytes_per_step": int(x0.numel() * 8), "d2h_bytes_per_step": int(x0.numel() * 8 + 8)}
+           "h2d_bytes_per_step": int(x0.numel() * 8), "d2h_bytes_per_step": int(x0.numel() * 8 + 8),
+           "call": "attn_eigsolve_host (pinned host tensor in and out, host wall clock)"}
+
+    # the accuracy-bearing form of the same solve: BF16 Lanczos then FP64 Rayleigh-Ritz
+    # refinement (3 Jacobi-Davidson corrections, FP64 contractions as split BF16 products)
+    solve = mixed_solve_record(attn, ctx, H, x0, torch)
 
     peaks, src = measured_peaks()
     achieved = (k_fl / k_n) / ((k_ms / k_n) / 1000.0) / 1e12 if k_n else None
-    peak = peaks["bf16_tflops_sustained"]
+    peak = peaks["bf16_tflops"]
+    traffic = profiled_traffic()
     roof = {"bound": "tensor", "kernel": "sandwich_tc_kernel", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": profiled_traffic(),
-            "peak_source": f"{src} bf16_tflops_sustained",
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, from "
+                               "profiles/sandwich_tc_kernel_tfim32x32_m128.md (same kernel source)") if traffic else None,
+            "peak_source": f"{src} bf16_tflops (burst: the kernel is timed per launch at full clock)",
             "flops_per_launch": k_fl / k_n if k_n else None, "avg_launch_ms": k_ms / k_n if k_n else None,
             "launches": k_n}
     line = {"metric": "H_eff matvecs/s at m=128", "value": value, "unit": "matvec/s", "n_gpus": world,
@@ -742,9 +906,12 @@ def main():
                        "lanczos_depth": DEPTH, "algorithmic_flops_per_matvec": flops_mv,
                        "l2": "256 MB buffer written between timed steps; Lanczos basis 336 MB > L2",
                        "parallelism": f"replicas{world}"},
-            "roofline": roof, "gpu_launches": int(launches), "e2e": e2e, "clocks": clk.summary()}
+            "roofline": roof, "gpu_launches": int(launches), "e2e": e2e, "clocks": clk.summary(),
+            "mixed_solve": solve}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(counts)
+        line["cpu_baseline"] = cpu_baseline(oracle_node_structure())
+    if rank == 0 and world == 1 and not args.no_sweep:
+        line["sweep"] = sweep_record(attn, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
     attn.attn_heff_destroy(H)

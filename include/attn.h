@@ -96,7 +96,13 @@ typedef struct {
   int wait_limit_log2;      /* consumer-side wait limit of the tensor-core H_eff kernel, 2^k clock cycles;
                                0 = the default of about 2 s. A short limit makes the kernel give up,
                                drain its copies and report ATTN_ETIMEOUT: for testing failure handling (0) */
-  int reserved[3];
+  int compress_terms;       /* sum the mapped terms of H' that act on the same sites into one term before the
+                               rank-1 split (the compression of Sec. 6.2.2: the xx, yy and zz terms of a bond
+                               mapped through one disentangler give one term of bond dimension <= d^2 instead of
+                               three); the same linear map with fewer products (0) */
+  int de_method;            /* disentangler optimisation: 0 = MERA-like self-consistent update (Sec. 4.1.1),
+                               1 = Riemannian conjugate gradients of the true E_k on O(4) (Sec. 4.1.2) (0) */
+  int reserved[1];
 } attn_config;
 
 ATTN_API attn_status attn_config_default(attn_config* cfg);
@@ -120,6 +126,23 @@ ATTN_API attn_status attn_get_config(attn_ctx* ctx, attn_config* cfg);
 /* Block until all work enqueued by the context has finished; ATTN_ETIMEOUT if a
  * bounded wait in the split FP64 GEMM gave up meanwhile (its error word is then cleared). */
 ATTN_API attn_status attn_sync(attn_ctx* ctx);
+/* Device memory from the caller (e.g. a framework's caching allocator). After
+ * attn_set_allocator(alloc, free, user) every device buffer the library allocates
+ * -- handle storage and the contexts' scratch -- comes from alloc(bytes, device,
+ * user), which must return a 256-byte aligned block of at least `bytes` on the
+ * current device (or NULL: the call fails with ATTN_ENOMEM), and goes back through
+ * free(ptr, bytes, device, user) of the allocator that served it, after the library
+ * has synchronised the device (as cudaFree would). (NULL, NULL, NULL) restores
+ * cudaMalloc/cudaFree. The setting is process-wide and applies to allocations made
+ * after the call; buffers allocated before it are returned to where they came
+ * from. Install it before creating contexts; the callbacks may be called from any
+ * library call until every handle is destroyed. The allocation-free entry point
+ * attn_heff_apply_f64_static never allocates and is unaffected. No counterpart in
+ * the paper: ownership of device memory is the host framework's. */
+typedef void* (*attn_alloc_fn)(size_t bytes, int device, void* user);
+typedef void (*attn_free_fn)(void* ptr, size_t bytes, int device, void* user);
+ATTN_API attn_status attn_set_allocator(attn_alloc_fn alloc, attn_free_fn free_fn, void* user);
+
 /* Number of library kernels launched by this context so far. */
 ATTN_API attn_status attn_kernel_launches(attn_ctx* ctx, uint64_t* count);
 /* Timing for measurement tools. enable != 0 clears the records and makes the
@@ -187,6 +210,34 @@ ATTN_API attn_status attn_node_device_ptr(attn_state* st, int node, double** dev
 ATTN_API attn_status attn_move_centre(attn_state* st, int node);
 /* max ||T^T T - 1|| over non-centre tensors (towards the centre). */
 ATTN_API attn_status attn_isometry_error(attn_state* st, double* err);
+
+/* Renormalise the effective operators across the link `slot` of `node` (Fig.
+ * eff-op, Fig. iso): the isometry centre moves to the neighbour n' on that link
+ * (one QR per link crossed; node must not be a lowest-layer tensor's site link),
+ * and the operators of every rank-1 product of H' with sites behind node, as seen
+ * from n', are built from node's two other links by O_out = T^T (O_x (x) O_y) T:
+ * products that lie entirely behind the link are summed into one internal
+ * operator, the others stay open (one operator each). *n_open (may be NULL)
+ * receives the number of open products. Requires attn_map_hamiltonian. */
+ATTN_API attn_status attn_renormalise(attn_state* st, int node, int slot, int* n_open);
+/* Effective operators of link (node, slot) as seen from node (computed if stale;
+ * the isometry centre must not lie behind that link): *dim the link dimension,
+ * *n_open the number of open products, *has_internal whether an internal operator
+ * exists; h_int (may be NULL) receives the internal operator (dim x dim row-major,
+ * zeros if none). Synchronous. */
+ATTN_API attn_status attn_link_operators(attn_state* st, int node, int slot, int* dim, int* n_open,
+                                         int* has_internal, double* h_int);
+
+/* --------------------------------------------------------------- persistence */
+
+/* Write / read everything a run resumes from: tensors, isometry centre,
+ * disentangler placement and matrices, sweep count, the known FP64 energy and the
+ * learned-start records (binary file, FP64 little-endian; the model is not stored,
+ * only a fingerprint of its terms). attn_state_load reads into a state of the same
+ * model and bond dimension (ATTN_EINVAL on any mismatch); effective operators are
+ * rebuilt on demand, so a resumed run repeats the original one's arithmetic. */
+ATTN_API attn_status attn_state_save(attn_state* st, const char* path);
+ATTN_API attn_status attn_state_load(attn_state* st, const char* path);
 
 /* ------------------------------------------------------------ disentanglers */
 
@@ -277,6 +328,10 @@ ATTN_API attn_status attn_heff_apply_f64_static(const attn_heff_desc* desc, cons
  * *theta the Ritz value. Matvecs in the context's matvec_dtype; when that is
  * not FP64, refine_steps FP64 residual corrections follow. *iters may be NULL. */
 ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, int* iters);
+/* attn_eigsolve on a HOST tensor: T_host [m0][m1][m2] is copied to a device buffer
+ * owned by h, solved there, and the Ritz vector copied back into T_host
+ * (synchronous). */
+ATTN_API attn_status attn_eigsolve_host(attn_heff* h, double* T_host, double* theta, int* iters);
 
 /* ----------------------------------------------------------- sweep drivers */
 
@@ -288,19 +343,49 @@ ATTN_API attn_status attn_ttn_sweep(attn_state* st, double* energy);
 /* Energy <T|H_eff|T> at the centre (FP64). */
 ATTN_API attn_status attn_energy(attn_state* st, double* energy);
 
-/* MERA-like update of every placed disentangler for the current TTN
- * (Sec. 4.1.1, Eqs. contracted and cost function): the environments (the
+/* Update of every placed disentangler for the current TTN. The environments (the
  * TTN's reduced density matrices on each disentangler's terms, Sec. 4.2) are
- * contracted once on the GPU; then, per disentangler, Gamma_k with u^T fixed,
- * u = -V W^T from the SVD Gamma_k = W sigma V^T, accepted while the true E_k
- * does not increase, up to de_max_iter steps or a relative change below
- * de_rel_dev. Terms are shifted by their spectral norm (reading: the paper
- * gives no shift). All disentanglers are independent given the TTN
- * (restriction 1) and are updated in one batch. *dE (may be NULL) receives
- * sum_k [E_k(new) - E_k(old)]. The mapped Hamiltonian is marked stale. */
+ * contracted once on the GPU; all disentanglers are independent given the TTN
+ * (restriction 1) and are updated in one batch, each by:
+ *  - de_method 0 (default), the MERA-like update (Sec. 4.1.1, Eqs. contracted
+ *    and cost function): Gamma_k with u^T fixed, u = -V W^T from the SVD
+ *    Gamma_k = W sigma V^T, accepted while the true E_k does not increase; terms
+ *    are shifted by their spectral norm (reading: the paper gives no shift);
+ *  - de_method 1, Riemannian conjugate gradients of the true E_k(u) on O(4)
+ *    (Sec. 4.1.2): Polak-Ribiere+ directions, QR retraction, Armijo steps;
+ * up to de_max_iter steps or a relative change below de_rel_dev. *dE (may be
+ * NULL) receives sum_k [E_k(new) - E_k(old)]. The mapped Hamiltonian is marked
+ * stale. */
 ATTN_API attn_status attn_de_update(attn_state* st, double* dE);
 /* E_k before and after the last attn_de_update, 2 doubles per disentangler. */
 ATTN_API attn_status attn_de_energies(attn_state* st, double* e_out);
+/* The same update for disentangler k alone: its environments only, the others
+ * unchanged (restriction 1 makes the updates independent). */
+ATTN_API attn_status attn_de_update_one(attn_state* st, int k, double* dE);
+/* Environment of disentangler k at a given orthogonal u (row-major 4 x 4): gamma16
+ * receives Gamma_k with E = Tr(u Gamma_k) for u^T fixed at u (Eq. contracted, terms
+ * shifted by their spectral norm), *e_k the true E_k(u) (Sec. 4.1.1). */
+ATTN_API attn_status attn_de_environment(attn_state* st, int k, const double* u16, double* gamma16, double* e_k);
+/* Two-site reduced density matrix of the TTN on disentangler k's sites (i, j),
+ * row-major 4 x 4 with site i most significant: the environment the update and
+ * the learned start read. */
+ATTN_API attn_status attn_rdm2(attn_state* st, int k, double* rho16);
+
+/* ------------------------------------------------------------- observables */
+
+/* Expectation values <psi_aTTN| o |psi_aTTN> (Sec. 5, Eq. obs) of products of
+ * one-site operators: observable q acts on nsites[q] in 1..4 distinct sites
+ * sites[4q .. 4q+nsites[q]-1] with the real 2 x 2 operators ops[16q + 4a ..]
+ * (row-major) on site a. Each is mapped through the disentangler layer (o' =
+ * D^T o D, the Hamiltonian's convention: an observable on n sites spans at most
+ * 2n after the mapping) and measured on the TTN. values receives n_obs doubles.
+ * Synchronous. */
+ATTN_API attn_status attn_measure(attn_state* st, int n_obs, const int* nsites, const int* sites, const double* ops,
+                                  double* values);
+/* Two-body correlation matrix of Eq. corrmat: C[i][j] = <o^a_i o^b_j> over all
+ * sites (Hilbert order), the diagonal being <(o^a o^b)_i>; oa, ob are 2 x 2
+ * row-major, C receives N x N doubles row-major. */
+ATTN_API attn_status attn_correlation_matrix(attn_state* st, const double* oa, const double* ob, double* C);
 /* One aTTN sweep (Sec. 4): if s_ttn sweeps have been done and disentanglers
  * are placed, update all disentanglers; map H -> H' if needed; then one TTN
  * sweep under H'. *energy receives the last local energy (= E of the state). */

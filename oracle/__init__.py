@@ -19,5 +19,7 @@ Parity status per module (what pins it is listed in each module header):
   lanczos       pinned (dense eigensolver of the same operator)
   sweep         pinned (exact case m >= 2^(N/2) reaches ED; variational bound)
   de_update     pinned (dense-state RDMs, optimality Tr(u Gamma) = -sum sigma)
-  mlp           pinned (finite differences; expm orthogonality, series check)
+  mlp           pinned (finite differences; expm orthogonality, series check;
+                Adam steps against hand-derived values)
+  observables   pinned (dense 16-site aTTN state; correlation-matrix symmetry)
 """

@@ -161,3 +161,72 @@ def optimise_de(problem, u0, max_iter=20, rel_dev=1e-12):
         if done:
             break
     return u, hist
+
+
+# ------------------------------------------------ Riemannian gradient descent
+# Sec. 4.1.2: both u and u^T vary; the cost is the true E_k(u) on the orthogonal
+# group. Reading (the paper names the approach, not its parameters): Riemannian
+# conjugate gradients in the embedded metric, Polak-Ribiere+ directions carried to
+# the new point by projection, the QR retraction R_u(xi) = qf(u + xi) (positive
+# diagonal of R), Armijo backtracking (c1 = 1e-4, halving) from a step of Frobenius
+# norm 0.25 (doubled after an accepted step, at most 1), the same stopping rule as
+# the MERA-like update (relative change below rel_dev, or max_iter steps).
+
+def euclidean_gradient(problem, u):
+    """dE_k/du = sum_p Tr_extra[2 h_p U rho_p], U = u (x) 1 on S'_p (h_p, rho_p symmetric)."""
+    i, j = problem.de
+    g = np.zeros((4, 4))
+    for (sp, h, _), r in zip(problem.terms, problem.rho):
+        U = embed(u, (i, j), sp)
+        g += partial_trace_keep(2.0 * h @ U @ r, sp, (i, j))
+    return g
+
+
+def tangent(u, z):
+    """Projection of z onto the tangent space of O(4) at u: u skew(u^T z)."""
+    a = u.T @ z
+    return u @ (0.5 * (a - a.T))
+
+
+def retract(u, xi):
+    q, r = np.linalg.qr(u + xi)
+    return q * np.sign(np.diag(r))
+
+
+def optimise_de_riemannian(problem, u0, max_iter=20, rel_dev=1e-12):
+    """Riemannian conjugate-gradient minimisation of E_k over O(4). Returns (u, E_k history)."""
+    u = u0.copy()
+    e = problem.energy(u)
+    hist = [e]
+    g = tangent(u, euclidean_gradient(problem, u))
+    d = -g
+    step = 0.25
+    for _ in range(max_iter):
+        gd = float(np.sum(g * d))
+        if not gd < 0.0:
+            d, gd = -g, -float(np.sum(g * g))
+        dn = float(np.linalg.norm(d))
+        if dn == 0.0:
+            break
+        t = step / dn
+        accepted = False
+        for _ in range(40):
+            un = retract(u, t * d)
+            en = problem.energy(un)
+            if en <= e + 1e-4 * t * gd:
+                accepted = True
+                break
+            t *= 0.5
+        if not accepted:
+            break
+        step = min(1.0, 2.0 * t * dn)
+        gn = tangent(un, euclidean_gradient(problem, un))
+        g_old = tangent(un, g)
+        d_old = tangent(un, d)
+        beta = max(0.0, float(np.sum(gn * (gn - g_old))) / max(float(np.sum(g * g)), 1e-300))
+        done = abs(en - e) <= rel_dev * max(abs(e), 1e-300)
+        u, e, g, d = un, en, gn, -gn + beta * d_old
+        hist.append(e)
+        if done:
+            break
+    return u, hist

@@ -32,7 +32,8 @@ class attn_config(ctypes.Structure):
                 ("refine_steps", ctypes.c_int), ("refine_tol", ctypes.c_double),
                 ("use_graphs", ctypes.c_int), ("refine_inner", ctypes.c_int),
                 ("f64_split", ctypes.c_int), ("report_unconverged", ctypes.c_int),
-                ("wait_limit_log2", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("wait_limit_log2", ctypes.c_int), ("compress_terms", ctypes.c_int),
+                ("de_method", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class attn_heff_desc(ctypes.Structure):
@@ -104,7 +105,23 @@ _SIGS = {
     "attn_de_training_pairs": [_P, _PD, _PD],
     "attn_learned_init_report": [_P, _PI, _PI],
     "attn_heff_apply_f64_static": [ctypes.POINTER(attn_heff_desc), _P, _P, _P],
+    "attn_set_allocator": [_P, _P, _P],
+    "attn_renormalise": [_P, _I, _I, _PI],
+    "attn_link_operators": [_P, _I, _I, _PI, _PI, _PI, _PD],
+    "attn_state_save": [_P, ctypes.c_char_p],
+    "attn_state_load": [_P, ctypes.c_char_p],
+    "attn_eigsolve_host": [_P, _PD, _PD, _PI],
+    "attn_de_update_one": [_P, _I, _PD],
+    "attn_de_environment": [_P, _I, _PD, _PD, _PD],
+    "attn_rdm2": [_P, _I, _PD],
+    "attn_measure": [_P, _I, _PI, _PI, _PD, _PD],
+    "attn_correlation_matrix": [_P, _PD, _PD, _PD],
 }
+
+# C callback types of attn_set_allocator
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
+_allocator_refs = []  # callbacks stay referenced while the library may call them
 
 _lib = None
 
@@ -538,3 +555,93 @@ def attn_learned_init_report(st):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(load().attn_learned_init_report(st, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+# ----------------------------------------------------------- boundary additions
+def attn_set_allocator(alloc=None, free=None):
+    """Install Python callables alloc(bytes, device) -> address and free(address, bytes,
+    device) as the library's device allocator (None, None: back to cudaMalloc)."""
+    if alloc is None:
+        _check(load().attn_set_allocator(None, None, None))
+        return
+    a = ALLOC_FN(lambda n, dev, user: alloc(n, dev))
+    f = FREE_FN(lambda p, n, dev, user: free(p, n, dev))
+    _allocator_refs.append((a, f))
+    _check(load().attn_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None))
+
+
+def attn_renormalise(st, node, slot):
+    n = ctypes.c_int()
+    _check(load().attn_renormalise(st, node, slot, ctypes.byref(n)))
+    return n.value
+
+
+def attn_link_operators(st, node, slot):
+    """(dim, n_open, has_internal, internal operator [dim, dim])."""
+    d, n, h = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().attn_link_operators(st, node, slot, ctypes.byref(d), None, None, None))
+    out = np.zeros((d.value, d.value))
+    _check(load().attn_link_operators(st, node, slot, ctypes.byref(d), ctypes.byref(n), ctypes.byref(h),
+                                      out.ctypes.data_as(_PD)))
+    return d.value, n.value, bool(h.value), out
+
+
+def attn_state_save(st, path):
+    _check(load().attn_state_save(st, os.fsencode(path)))
+
+
+def attn_state_load(st, path):
+    _check(load().attn_state_load(st, os.fsencode(path)))
+
+
+def attn_eigsolve_host(h, T_host):
+    """Eigensolve on a host float64 C-contiguous array, updated in place with the Ritz vector."""
+    assert T_host.dtype == np.float64 and T_host.flags.c_contiguous
+    th, it = ctypes.c_double(), ctypes.c_int()
+    _check(load().attn_eigsolve_host(h, T_host.ctypes.data_as(_PD), ctypes.byref(th), ctypes.byref(it)))
+    return th.value, it.value
+
+
+def attn_de_update_one(st, k):
+    d = ctypes.c_double()
+    _check(load().attn_de_update_one(st, k, ctypes.byref(d)))
+    return d.value
+
+
+def attn_de_environment(st, k, u):
+    ua, up = _host_d(np.asarray(u).reshape(16))
+    g = np.zeros(16)
+    e = ctypes.c_double()
+    _check(load().attn_de_environment(st, k, up, g.ctypes.data_as(_PD), ctypes.byref(e)))
+    return g.reshape(4, 4), e.value
+
+
+def attn_rdm2(st, k):
+    r = np.zeros(16)
+    _check(load().attn_rdm2(st, k, r.ctypes.data_as(_PD)))
+    return r.reshape(4, 4)
+
+
+def attn_measure(st, observables):
+    """``observables``: list of (sites, [2x2 operators]) with 1..4 distinct sites each."""
+    n = len(observables)
+    ns = np.zeros(max(n, 1), dtype=np.int32)
+    sites = np.zeros(4 * max(n, 1), dtype=np.int32)
+    ops = np.zeros(16 * max(n, 1))
+    for q, (s, o) in enumerate(observables):
+        ns[q] = len(s)
+        sites[4 * q:4 * q + len(s)] = s
+        for a, m in enumerate(o):
+            ops[16 * q + 4 * a:16 * q + 4 * a + 4] = np.asarray(m, dtype=np.float64).reshape(4)
+    out = np.zeros(max(n, 1))
+    _check(load().attn_measure(st, n, ns.ctypes.data_as(_PI), sites.ctypes.data_as(_PI), ops.ctypes.data_as(_PD),
+                               out.ctypes.data_as(_PD)))
+    return out[:n]
+
+
+def attn_correlation_matrix(st, oa, ob, n_sites):
+    a, ap = _host_d(np.asarray(oa).reshape(4))
+    b, bp = _host_d(np.asarray(ob).reshape(4))
+    C = np.zeros((n_sites, n_sites))
+    _check(load().attn_correlation_matrix(st, ap, bp, C.ctypes.data_as(_PD)))
+    return C

@@ -41,16 +41,31 @@ struct Error {
 // Owning device buffer (cudaMalloc / cudaFree). A buffer that captured CUDA graphs
 // may reference carries an epoch counter, bumped whenever the buffer is
 // reallocated, so that graphs built on the old address can be detected.
+// Device memory comes from cudaMalloc, or from the caller's allocator installed with
+// attn_set_allocator; a buffer remembers which one served it and returns it there.
+struct Allocator {
+  attn_alloc_fn alloc = nullptr;
+  attn_free_fn free = nullptr;
+  void* user = nullptr;
+};
+const Allocator* current_allocator();  // nullptr: cudaMalloc / cudaFree
+void set_allocator(attn_alloc_fn alloc, attn_free_fn free_fn, void* user);
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
   uint64_t* epoch = nullptr;  // not owned; bumped on every reallocation
+  const Allocator* from = nullptr;  // allocator that served p (nullptr: cudaMalloc)
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), from(o.from) { o.p = nullptr; o.bytes = 0; }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    if (this != &o) {
+      release();
+      p = o.p; bytes = o.bytes; from = o.from;
+      o.p = nullptr; o.bytes = 0;
+    }
     return *this;
   }
   ~DevBuf() { release(); }
@@ -198,5 +213,8 @@ std::vector<std::pair<int, int>> place_disentanglers(const Tree& T, const Model&
 std::vector<Term> map_terms(const Model& M, const std::vector<std::pair<int, int>>& des,
                             const std::vector<std::vector<double>>& us);
 std::vector<Prod> split_products(const std::vector<Term>& terms);
+// One term per distinct site set: the operators of terms on the same sites summed
+// (same linear map, fewer rank-1 products after the split).
+std::vector<Term> compress_terms(const std::vector<Term>& terms);
 
 }  // namespace attn

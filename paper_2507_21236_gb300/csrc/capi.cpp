@@ -2,6 +2,7 @@
 // Every entry point converts internal exceptions into an attn_status and a
 // thread-local message; nothing throws across the boundary.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -25,10 +26,34 @@ void set_error(const char* fmt, ...) {
 void clear_error() { g_err.clear(); }
 const char* last_error() { return g_err.c_str(); }
 
+// The allocator installed by attn_set_allocator. Records are never freed: a buffer
+// keeps a pointer to the one that served it until the buffer is released.
+static std::atomic<const Allocator*> g_allocator{nullptr};
+const Allocator* current_allocator() { return g_allocator.load(); }
+void set_allocator(attn_alloc_fn alloc, attn_free_fn free_fn, void* user) {
+  if (!alloc) {
+    g_allocator.store(nullptr);
+    return;
+  }
+  g_allocator.store(new Allocator{alloc, free_fn, user});
+}
+
 void DevBuf::release() {
-  if (p) cudaFree(p);
+  if (p) {
+    if (from) {
+      // cudaFree waits for the device before it returns memory; a caller's allocator
+      // may hand the block out again at once, so wait here for kernels still using it
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceSynchronize();
+      from->free(p, bytes, dev, from->user);
+    } else {
+      cudaFree(p);
+    }
+  }
   p = nullptr;
   bytes = 0;
+  from = nullptr;
 }
 
 void DevBuf::reserve(size_t n) {
@@ -36,12 +61,23 @@ void DevBuf::reserve(size_t n) {
   release();
   if (epoch) ++*epoch;
   size_t want = std::max<size_t>(n, 256);
-  cudaError_t e = cudaMalloc(&p, want);
-  if (e != cudaSuccess) {
-    p = nullptr;
-    (void)cudaGetLastError();
-    throw Error{ATTN_ENOMEM, std::string("cudaMalloc of ") + std::to_string(want) + " bytes failed: " +
-                                 cudaGetErrorString(e)};
+  const Allocator* a = current_allocator();
+  if (a) {
+    int dev = 0;
+    ATTN_CHECK_CUDA(cudaGetDevice(&dev));
+    p = a->alloc(want, dev, a->user);
+    ATTN_REQUIRE(p != nullptr, ATTN_ENOMEM,
+                 "the caller's allocator returned NULL for " + std::to_string(want) + " bytes");
+    ATTN_REQUIRE(((uintptr_t)p & 255) == 0, ATTN_EINVAL, "the caller's allocator must return 256-byte aligned blocks");
+    from = a;
+  } else {
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      (void)cudaGetLastError();
+      throw Error{ATTN_ENOMEM, std::string("cudaMalloc of ") + std::to_string(want) + " bytes failed: " +
+                                   cudaGetErrorString(e)};
+    }
   }
   bytes = want;
 }
@@ -185,6 +221,7 @@ ATTN_API attn_status attn_set_config(attn_ctx* ctx, const attn_config* cfg) {
   ATTN_REQUIRE(cfg->matvec_dtype == ATTN_F64 || cfg->matvec_dtype == ATTN_BF16, ATTN_EUNSUPPORTED,
                "matvec_dtype must be ATTN_F64 or ATTN_BF16");
   ATTN_REQUIRE(cfg->wait_limit_log2 >= 0 && cfg->wait_limit_log2 <= 62, ATTN_EINVAL, "wait_limit_log2 must be 0..62");
+  ATTN_REQUIRE(cfg->de_method == 0 || cfg->de_method == 1, ATTN_EINVAL, "de_method must be 0 or 1");
   ctx->cfg = *cfg;
   ATTN_CATCH
 }
@@ -603,11 +640,10 @@ ATTN_API attn_status attn_heff_apply_host(attn_heff* h, const double* xh, double
   ATTN_CATCH
 }
 
-ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, int* iters) {
-  ATTN_TRY
-  NEED(h, "heff");
-  NEED(T_dev, "T_dev");
-  NEED(theta, "theta");
+}  // extern "C"
+
+// Lowest eigenpair of H_eff from the device tensor T_dev (the body of attn_eigsolve).
+static void eigsolve_dev(attn_heff* h, double* T_dev, double* theta, int* iters) {
   attn_ctx* ctx = h->ctx;
   const attn_config& cfg = ctx->cfg;
   // shapes the tensor-core tiles cannot take run their matvecs in FP64 (on the GPU)
@@ -702,7 +738,7 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
     if (iters) *iters = it;
     ATTN_REQUIRE(!(cfg.report_unconverged && !conv), ATTN_ENOTCONVERGED,
                  "the eigensolve stopped above its tolerance (best Ritz pair written)");
-    return ATTN_OK;
+    return;
   }
   LanczosWork w;
   LanczosResult r = timeout_first(ctx, h, [&] {
@@ -726,6 +762,31 @@ ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, i
   if (iters) *iters = it;
   ATTN_REQUIRE(!(cfg.report_unconverged && !conv), ATTN_ENOTCONVERGED,
                "the eigensolve stopped above its tolerance (best Ritz pair written)");
+}
+
+extern "C" {
+
+ATTN_API attn_status attn_eigsolve(attn_heff* h, double* T_dev, double* theta, int* iters) {
+  ATTN_TRY
+  NEED(h, "heff");
+  NEED(T_dev, "T_dev");
+  NEED(theta, "theta");
+  eigsolve_dev(h, T_dev, theta, iters);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_eigsolve_host(attn_heff* h, double* T_host, double* theta, int* iters) {
+  ATTN_TRY
+  NEED(h, "heff");
+  NEED(T_host, "T_host");
+  NEED(theta, "theta");
+  attn_ctx* ctx = h->ctx;
+  h->host_x.reserve(sizeof(double) * h->V);  // owned by h: a stable address for graph replays
+  double* xd = h->host_x.as<double>();
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(xd, T_host, sizeof(double) * h->V, cudaMemcpyHostToDevice, ctx->stream));
+  eigsolve_dev(h, xd, theta, iters);
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(T_host, xd, sizeof(double) * h->V, cudaMemcpyDeviceToHost, ctx->stream));
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
   ATTN_CATCH
 }
 
@@ -753,7 +814,7 @@ ATTN_API attn_status attn_de_update(attn_state* st, double* dE) {
   ATTN_TRY
   NEED(st, "state");
   st->ctx->prof_begin(8);
-  double d = st->de_update(nullptr, nullptr);
+  double d = st->de_update(nullptr);
   st->ctx->prof_end(8, 0.0);
   if (dE) *dE = d;
   ATTN_CATCH
@@ -773,7 +834,7 @@ ATTN_API attn_status attn_sweep(attn_state* st, double* energy) {
   const attn_config& cfg = st->ctx->cfg;
   if (st->sweep_count >= cfg.s_ttn && !st->des.empty()) {
     st->ctx->prof_begin(8);
-    st->de_update(nullptr, nullptr);
+    st->de_update(nullptr);
     st->ctx->prof_end(8, 0.0);
   }
   if (!st->mapped_ready) st->set_products();
@@ -929,6 +990,146 @@ ATTN_API attn_status attn_energy(attn_state* st, double* energy) {
   NEED(st, "state");
   NEED(energy, "energy");
   *energy = st->energy();
+  ATTN_CATCH
+}
+
+
+// ----------------------------------------------------- boundary additions
+ATTN_API attn_status attn_set_allocator(attn_alloc_fn alloc, attn_free_fn free_fn, void* user) {
+  ATTN_TRY
+  ATTN_REQUIRE((alloc == nullptr) == (free_fn == nullptr), ATTN_EINVAL, "give both alloc and free, or neither");
+  set_allocator(alloc, free_fn, user);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_renormalise(attn_state* st, int node, int slot, int* n_open) {
+  ATTN_TRY
+  NEED(st, "state");
+  ATTN_REQUIRE(node >= 0 && node < st->tree.n_nodes && slot >= 0 && slot < 3, ATTN_EINVAL, "node/slot out of range");
+  ATTN_REQUIRE(st->mapped_ready, ATTN_EINVAL, "Hamiltonian not mapped yet (call attn_map_hamiltonian)");
+  const Tree::Nbr& nb = st->tree.nbr[3 * node + slot];
+  ATTN_REQUIRE(nb.kind == 1, ATTN_EINVAL, "the link leads to a physical site, not to a tensor");
+  st->move_centre(nb.idx);
+  const Env& e = st->get_env(nb.idx, nb.back);
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  if (n_open) *n_open = (int)e.open.size();
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_link_operators(attn_state* st, int node, int slot, int* dim, int* n_open, int* has_internal,
+                                         double* h_int) {
+  ATTN_TRY
+  NEED(st, "state");
+  ATTN_REQUIRE(node >= 0 && node < st->tree.n_nodes && slot >= 0 && slot < 3, ATTN_EINVAL, "node/slot out of range");
+  const Env& e = st->get_env(node, slot);
+  if (dim) *dim = e.dim;
+  if (n_open) *n_open = (int)e.open.size();
+  if (has_internal) *has_internal = e.has_hint ? 1 : 0;
+  if (h_int) {
+    const size_t n = (size_t)e.dim * e.dim;
+    if (e.has_hint)
+      ATTN_CHECK_CUDA(cudaMemcpyAsync(h_int, e.hint.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st->ctx->stream));
+    else
+      std::fill(h_int, h_int + n, 0.0);
+  }
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_state_save(attn_state* st, const char* path) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(path, "path");
+  st->save(path);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_state_load(attn_state* st, const char* path) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(path, "path");
+  st->load(path);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_de_update_one(attn_state* st, int k, double* dE) {
+  ATTN_TRY
+  NEED(st, "state");
+  ATTN_REQUIRE(k >= 0 && k < (int)st->des.size(), ATTN_EINVAL, "disentangler index out of range");
+  const std::vector<int> one = {k};
+  st->ctx->prof_begin(8);
+  const double d = st->de_update(&one);
+  st->ctx->prof_end(8, 0.0);
+  if (dE) *dE = d;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_de_environment(attn_state* st, int k, const double* u16, double* gamma16, double* e_k) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(u16, "u16");
+  ATTN_REQUIRE(k >= 0 && k < (int)st->des.size(), ATTN_EINVAL, "disentangler index out of range");
+  double g[16], e = 0.0;
+  st->de_environment(k, u16, g, &e);
+  if (gamma16) std::copy(g, g + 16, gamma16);
+  if (e_k) *e_k = e;
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_rdm2(attn_state* st, int k, double* rho16) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(rho16, "rho16");
+  ATTN_REQUIRE(k >= 0 && k < (int)st->des.size(), ATTN_EINVAL, "disentangler index out of range");
+  const std::vector<double> r = st->de_rdms({k});
+  std::copy(r.begin(), r.end(), rho16);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_measure(attn_state* st, int n_obs, const int* nsites, const int* sites, const double* ops,
+                                  double* values) {
+  ATTN_TRY
+  NEED(st, "state");
+  ATTN_REQUIRE(n_obs >= 0, ATTN_EINVAL, "n_obs < 0");
+  if (!n_obs) return ATTN_OK;
+  NEED(nsites, "nsites");
+  NEED(sites, "sites");
+  NEED(ops, "ops");
+  NEED(values, "values");
+  const std::vector<double> v = st->measure(n_obs, nsites, sites, ops);
+  std::copy(v.begin(), v.end(), values);
+  ATTN_CATCH
+}
+
+ATTN_API attn_status attn_correlation_matrix(attn_state* st, const double* oa, const double* ob, double* C) {
+  ATTN_TRY
+  NEED(st, "state");
+  NEED(oa, "oa");
+  NEED(ob, "ob");
+  NEED(C, "C");
+  const int N = st->model.n_sites;
+  std::vector<int> ns((size_t)N * N), sites(4L * N * N, 0);
+  std::vector<double> ops(16L * N * N, 0.0);
+  double ab[4];  // o^a o^b on one site
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c) ab[r * 2 + c] = oa[r * 2] * ob[c] + oa[r * 2 + 1] * ob[2 + c];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      const long q = (long)i * N + j;
+      if (i == j) {
+        ns[q] = 1;
+        sites[4 * q] = i;
+        std::copy(ab, ab + 4, ops.begin() + 16 * q);
+      } else {
+        ns[q] = 2;
+        sites[4 * q] = i;
+        sites[4 * q + 1] = j;
+        std::copy(oa, oa + 4, ops.begin() + 16 * q);
+        std::copy(ob, ob + 4, ops.begin() + 16 * q + 4);
+      }
+    }
+  const std::vector<double> v = st->measure(N * N, ns.data(), sites.data(), ops.data());
+  std::copy(v.begin(), v.end(), C);
   ATTN_CATCH
 }
 

@@ -203,6 +203,117 @@ __global__ void de_mera_kernel(DEArgs a) {
   a.e_out[2 * k + 1] = e;
 }
 
+// ---- Riemannian conjugate gradients on O(4) (Sec. 4.1.2): the true E_k(u) with u
+// and u^T varying together. With E = sum_q Tr(M_q u^T C_q u), the Euclidean gradient
+// is sum_q (C_q u M_q + C_q^T u M_q^T); it is projected onto the tangent space
+// u skew(u^T G); Polak-Ribiere+ directions are carried to the new point by the same
+// projection; the retraction is the Q factor (positive diagonal of R) of u + xi; the
+// step is found by Armijo backtracking (c1 = 1e-4, halving) from a Frobenius step
+// of 0.25, doubled after an accepted step up to 1. Stops like the MERA-like update.
+__device__ void de_egrad(const DEArgs& a, int b0, int b1, const double* u, double* g) {
+  double M[16], t1[16], t2[16];
+  for (int i = 0; i < 16; ++i) g[i] = 0.0;
+  for (int q = b0; q < b1; ++q) {
+    const double* C = a.ent_C + 16L * q;
+    for (int i = 0; i < 16; ++i) M[i] = a.vals[a.ent_midx[16L * q + i]];
+    mm4(C, u, t1);   // C u
+    mm4(t1, M, t2);  // C u M
+    for (int i = 0; i < 16; ++i) g[i] += t2[i];
+    mtm4(C, u, t1);  // C^T u
+    for (int r = 0; r < 4; ++r)  // (C^T u) M^T
+      for (int c = 0; c < 4; ++c) {
+        double acc = 0.0;
+        for (int k = 0; k < 4; ++k) acc += t1[r * 4 + k] * M[c * 4 + k];
+        g[r * 4 + c] += acc;
+      }
+  }
+}
+
+// u skew(u^T z)
+__device__ void de_tangent(const double* u, const double* z, double* out) {
+  double a[16], sk[16];
+  mtm4(u, z, a);
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) sk[r * 4 + c] = 0.5 * (a[r * 4 + c] - a[c * 4 + r]);
+  mm4(u, sk, out);
+}
+
+// Q of u + xi by Gram-Schmidt on the columns, applied twice (R's diagonal > 0)
+__device__ void de_retract(const double* u, const double* xi, double* q) {
+  for (int i = 0; i < 16; ++i) q[i] = u[i] + xi[i];
+  for (int c = 0; c < 4; ++c) {
+    for (int pass = 0; pass < 2; ++pass)
+      for (int o = 0; o < c; ++o) {
+        double d = 0.0;
+        for (int r = 0; r < 4; ++r) d += q[r * 4 + o] * q[r * 4 + c];
+        for (int r = 0; r < 4; ++r) q[r * 4 + c] -= d * q[r * 4 + o];
+      }
+    double n = 0.0;
+    for (int r = 0; r < 4; ++r) n += q[r * 4 + c] * q[r * 4 + c];
+    n = sqrt(n);
+    for (int r = 0; r < 4; ++r) q[r * 4 + c] /= n;
+  }
+}
+
+__device__ double dot16(const double* x, const double* y) {
+  double s = 0.0;
+  for (int i = 0; i < 16; ++i) s += x[i] * y[i];
+  return s;
+}
+
+__global__ void de_rgd_kernel(DEArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.n_de) return;
+  const int b0 = a.ent_begin[k], b1 = a.ent_begin[k + 1];
+  double u[16], g[16], d[16], un[16], gn[16], go[16], dn[16], z[16], xi[16];
+  for (int i = 0; i < 16; ++i) u[i] = a.u_in[16L * k + i];
+  double e = de_energy(a, b0, b1, u);
+  a.e_out[2 * k] = e;
+  de_egrad(a, b0, b1, u, z);
+  de_tangent(u, z, g);
+  for (int i = 0; i < 16; ++i) d[i] = -g[i];
+  double step = 0.25;
+  for (int it = 0; it < a.max_iter; ++it) {
+    double gd = dot16(g, d);
+    if (!(gd < 0.0)) {
+      for (int i = 0; i < 16; ++i) d[i] = -g[i];
+      gd = -dot16(g, g);
+    }
+    const double dnorm = sqrt(dot16(d, d));
+    if (dnorm == 0.0) break;
+    double t = step / dnorm, en = 0.0;
+    bool accepted = false;
+    for (int ls = 0; ls < 40; ++ls) {
+      for (int i = 0; i < 16; ++i) xi[i] = t * d[i];
+      de_retract(u, xi, un);
+      en = de_energy(a, b0, b1, un);
+      if (en <= e + 1e-4 * t * gd) {
+        accepted = true;
+        break;
+      }
+      t *= 0.5;
+    }
+    if (!accepted) break;
+    step = fmin(1.0, 2.0 * t * dnorm);
+    de_egrad(a, b0, b1, un, z);
+    de_tangent(un, z, gn);
+    de_tangent(un, g, go);
+    de_tangent(un, d, dn);
+    double gg = dot16(g, g);
+    double beta = fmax(0.0, (dot16(gn, gn) - dot16(gn, go)) / fmax(gg, 1e-300));
+    const bool done = fabs(en - e) <= a.rel_dev * fmax(fabs(e), 1e-300);
+    for (int i = 0; i < 16; ++i) {
+      u[i] = un[i];
+      g[i] = gn[i];
+      d[i] = -gn[i] + beta * dn[i];
+    }
+    e = en;
+    if (done) break;
+  }
+  for (int i = 0; i < 16; ++i) a.u_out[16L * k + i] = u[i];
+  a.e_out[2 * k + 1] = e;
+}
+
 // E_k of candidate disentanglers (one thread per disentangler)
 __global__ void de_energy_kernel(DEArgs a, const double* u_cand, double* e_out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -473,66 +584,79 @@ void attn_state::probe_expectations(const std::vector<ProbeFactor>& F, const std
 }
 
 // ------------------------------------------------------ disentangler update
-double attn_state::de_update(const std::vector<std::vector<double>>* u_start, std::vector<double>* rho_out) {
+// Probes and 4x4 coefficient blocks of the selected disentanglers (Sec. 4.1.1):
+// position q of `sel` owns entries ent_begin[q] .. ent_begin[q+1] and the matrix
+// units rho_idx[16 q ..] of its two-site density matrix.
+void attn_state::de_setup(const std::vector<int>& sel, DESetup& S) {
   const int nDE = (int)des.size();
-  if (!nDE) return 0.0;
+  const int nS = (int)sel.size();
+  S.sel = sel;
+  S.F.clear();
+  S.P.clear();
   std::vector<int> owner(model.n_sites, -1);
-  for (int k = 0; k < nDE; ++k) owner[des[k].first] = owner[des[k].second] = k;
-  std::vector<ProbeFactor> F;
-  std::vector<Probe> P;
-  // matrix units on every disentangler site: fid[k][side][x], x = a*2+b for |a><b|
-  std::vector<std::array<std::array<int, 4>, 2>> fid(nDE);
-  for (int k = 0; k < nDE; ++k)
+  for (int q = 0; q < nS; ++q) {
+    ATTN_REQUIRE(sel[q] >= 0 && sel[q] < nDE, ATTN_EINVAL, "disentangler index out of range");
+    owner[des[sel[q]].first] = owner[des[sel[q]].second] = q;
+  }
+  std::vector<ProbeFactor>& F = S.F;
+  std::vector<Probe>& P = S.P;
+  // matrix units on every selected disentangler site: fid[q][side][x], x = a*2+b for |a><b|
+  std::vector<std::array<std::array<int, 4>, 2>> fid(nS);
+  for (int q = 0; q < nS; ++q)
     for (int side = 0; side < 2; ++side)
       for (int x = 0; x < 4; ++x) {
         ProbeFactor f;
-        f.site = side ? des[k].second : des[k].first;
+        f.site = side ? des[sel[q]].second : des[sel[q]].first;
         for (int i = 0; i < 4; ++i) f.op[i] = (i == x) ? 1.0 : 0.0;
-        fid[k][side][x] = (int)F.size();
+        fid[q][side][x] = (int)F.size();
         F.push_back(f);
       }
   // M[alpha][beta] = < |beta><alpha| (x) extra >: the probe for (alpha, beta) has
   // |b_i><a_i| on i and |b_j><a_j| on j (x = b*2 + a), and `extra` (factor id or -1).
-  auto add_block = [&](int k, int extra, std::vector<int>& midx) {
+  auto add_block = [&](int q, int extra, std::vector<int>& midx) {
     midx.resize(16);
     for (int al = 0; al < 4; ++al)
       for (int be = 0; be < 4; ++be) {
         const int ai = al >> 1, aj = al & 1, bi = be >> 1, bj = be & 1;
         Probe p;
         p.n = extra >= 0 ? 3 : 2;
-        p.f[0] = fid[k][0][bi * 2 + ai];
-        p.f[1] = fid[k][1][bj * 2 + aj];
+        p.f[0] = fid[q][0][bi * 2 + ai];
+        p.f[1] = fid[q][1][bj * 2 + aj];
         p.f[2] = extra;
+        for (int e = 3; e < 8; ++e) p.f[e] = -1;
         midx[al * 4 + be] = (int)P.size();
         P.push_back(p);
       }
   };
-  std::vector<int> rho_idx(16L * nDE), ent_begin(nDE + 1, 0), ent_midx;
-  std::vector<double> ent_C, lambda(nDE, 0.0);
-  std::vector<std::vector<std::pair<std::vector<int>, std::vector<double>>>> ents(nDE);
-  for (int k = 0; k < nDE; ++k) {
+  S.rho_idx.assign(16L * nS, 0);
+  S.ent_begin.assign(nS + 1, 0);
+  S.ent_midx.clear();
+  S.ent_C.clear();
+  S.lambda.assign(nS, 0.0);
+  std::vector<std::vector<std::pair<std::vector<int>, std::vector<double>>>> ents(nS);
+  for (int q = 0; q < nS; ++q) {
     std::vector<int> m;
-    add_block(k, -1, m);
-    std::copy(m.begin(), m.end(), rho_idx.begin() + 16L * k);
+    add_block(q, -1, m);
+    std::copy(m.begin(), m.end(), S.rho_idx.begin() + 16L * q);
   }
   for (const Term& tm : model.terms) {
-    int k = -1;
+    int q = -1;
     for (int a = 0; a < tm.n; ++a)
-      if (owner[tm.site[a]] >= 0) k = owner[tm.site[a]];
-    if (k < 0) continue;
-    const int i = des[k].first, j = des[k].second;
+      if (owner[tm.site[a]] >= 0) q = owner[tm.site[a]];
+    if (q < 0) continue;
+    const int i = des[sel[q]].first, j = des[sel[q]].second;
     std::vector<int> sites(tm.site, tm.site + tm.n), extra;
     for (int s : sites)
       if (s != i && s != j) extra.push_back(s);
     ATTN_REQUIRE(extra.size() <= 1, ATTN_EUNSUPPORTED, "disentangler update supports terms with <= 1 extra site");
     {  // spectral norm of the term
-      std::vector<double> U, s, V;
+      std::vector<double> U, sv, V;
       const int D = 1 << tm.n;
-      small_svd(tm.op, D, D, U, s, V);
-      lambda[k] += *std::max_element(s.begin(), s.end());
+      small_svd(tm.op, D, D, U, sv, V);
+      S.lambda[q] += *std::max_element(sv.begin(), sv.end());
     }
     if (extra.empty()) {
-      ents[k].push_back({std::vector<int>(rho_idx.begin() + 16L * k, rho_idx.begin() + 16L * k + 16),
+      ents[q].push_back({std::vector<int>(S.rho_idx.begin() + 16L * q, S.rho_idx.begin() + 16L * q + 16),
                          embed_any(tm.op, sites, {i, j})});
       continue;
     }
@@ -544,95 +668,159 @@ double attn_state::de_update(const std::vector<std::vector<double>>* u_start, st
       for (int be = 0; be < 4; ++be)
         for (int ep = 0; ep < 2; ++ep)
           for (int eq = 0; eq < 2; ++eq) R[(al * 4 + be) * 4 + ep * 2 + eq] = h3[(al * 2 + ep) * 8 + be * 2 + eq];
-    std::vector<double> U, s, Vv;
-    small_svd(R, 16, 4, U, s, Vv);
-    const double smax = *std::max_element(s.begin(), s.end());
+    std::vector<double> U, sv, Vv;
+    small_svd(R, 16, 4, U, sv, Vv);
+    const double smax = *std::max_element(sv.begin(), sv.end());
     for (int r = 0; r < 4; ++r) {
-      if (!(s[r] > 1e-14 * smax)) continue;
+      if (!(sv[r] > 1e-14 * smax)) continue;
       ProbeFactor f;
       f.site = e;
-      for (int q = 0; q < 4; ++q) f.op[q] = Vv[q * 4 + r];
+      for (int c = 0; c < 4; ++c) f.op[c] = Vv[c * 4 + r];
       const int fidx = (int)F.size();
       F.push_back(f);
       std::vector<int> m;
-      add_block(k, fidx, m);
+      add_block(q, fidx, m);
       std::vector<double> C(16);
-      for (int q = 0; q < 16; ++q) C[q] = U[q * 4 + r] * s[r];
-      ents[k].push_back({m, C});
+      for (int c = 0; c < 16; ++c) C[c] = U[c * 4 + r] * sv[r];
+      ents[q].push_back({m, C});
     }
   }
-  for (int k = 0; k < nDE; ++k) {
-    ATTN_REQUIRE((int)ents[k].size() <= kMaxEnt, ATTN_EUNSUPPORTED, "too many terms on one disentangler");
-    ent_begin[k + 1] = ent_begin[k] + (int)ents[k].size();
-    for (auto& pr : ents[k]) {
-      ent_midx.insert(ent_midx.end(), pr.first.begin(), pr.first.end());
-      ent_C.insert(ent_C.end(), pr.second.begin(), pr.second.end());
+  for (int q = 0; q < nS; ++q) {
+    ATTN_REQUIRE((int)ents[q].size() <= kMaxEnt, ATTN_EUNSUPPORTED, "too many terms on one disentangler");
+    S.ent_begin[q + 1] = S.ent_begin[q] + (int)ents[q].size();
+    for (auto& pr : ents[q]) {
+      S.ent_midx.insert(S.ent_midx.end(), pr.first.begin(), pr.first.end());
+      S.ent_C.insert(S.ent_C.end(), pr.second.begin(), pr.second.end());
     }
   }
+}
+
+namespace attn {
+namespace {
+// Device copies of a DESetup's tables, and the kernel arguments pointing at them.
+struct DEDev {
+  DevBuf eb, em, ec, lam, rho, vals;
+};
+DEArgs de_upload(attn_ctx* ctx, const DESetup& S, DEDev& d) {
+  upload(ctx, d.eb, S.ent_begin.data(), sizeof(int) * S.ent_begin.size());
+  upload(ctx, d.em, S.ent_midx.data(), sizeof(int) * S.ent_midx.size());
+  upload(ctx, d.ec, S.ent_C.data(), sizeof(double) * S.ent_C.size());
+  upload(ctx, d.lam, S.lambda.data(), sizeof(double) * S.lambda.size());
+  upload(ctx, d.rho, S.rho_idx.data(), sizeof(int) * S.rho_idx.size());
+  DEArgs a;
+  a.n_de = (int)S.sel.size();
+  a.ent_begin = d.eb.as<int>();
+  a.ent_midx = d.em.as<int>();
+  a.ent_C = d.ec.as<double>();
+  a.lambda = d.lam.as<double>();
+  a.rho_idx = d.rho.as<int>();
+  a.vals = d.vals.as<double>();
+  a.u_in = a.u_out = nullptr;
+  a.e_out = nullptr;
+  a.max_iter = ctx->cfg.de_max_iter;
+  a.rel_dev = ctx->cfg.de_rel_dev;
+  return a;
+}
+
+// Gamma_k (shifted terms, Eq. contracted) and E_k at given disentanglers, one thread each.
+__global__ void de_gamma_kernel(DEArgs a, const double* u, double* g_out, double* e_out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.n_de) return;
+  const int b0 = a.ent_begin[k], b1 = a.ent_begin[k + 1];
+  de_gamma(a, k, b0, b1, u + 16L * k, g_out + 16L * k);
+  e_out[k] = de_energy(a, b0, b1, u + 16L * k);
+}
+}  // namespace
+}  // namespace attn
+
+std::vector<double> attn_state::de_rdms(const std::vector<int>& sel) {
+  DESetup S;
+  de_setup(sel, S);
   DevBuf vals;
-  probe_expectations(F, P, vals);
-  // device inputs
-  DevBuf d_eb, d_em, d_ec, d_lam, d_rho, d_uin, d_uout, d_e;
-  upload(ctx, d_eb, ent_begin.data(), sizeof(int) * ent_begin.size());
-  upload(ctx, d_em, ent_midx.data(), sizeof(int) * ent_midx.size());
-  upload(ctx, d_ec, ent_C.data(), sizeof(double) * ent_C.size());
-  upload(ctx, d_lam, lambda.data(), sizeof(double) * nDE);
-  upload(ctx, d_rho, rho_idx.data(), sizeof(int) * rho_idx.size());
-  std::vector<double> uin(16L * nDE);
-  const auto& u0 = u_start ? *u_start : us;
-  for (int k = 0; k < nDE; ++k) std::copy(u0[k].begin(), u0[k].end(), uin.begin() + 16L * k);
+  probe_expectations(S.F, S.P, vals);
+  std::vector<double> pv(S.P.size());
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(pv.data(), vals.p, sizeof(double) * pv.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  std::vector<double> rho(16L * sel.size());
+  for (size_t q = 0; q < rho.size(); ++q) rho[q] = pv[S.rho_idx[q]];
+  return rho;
+}
+
+void attn_state::de_environment(int k, const double* u16, double* gamma16, double* e_k) {
+  DESetup S;
+  de_setup({k}, S);
+  DEDev d;
+  probe_expectations(S.F, S.P, d.vals);
+  DEArgs a = de_upload(ctx, S, d);
+  DevBuf du, dg, de;
+  upload(ctx, du, u16, sizeof(double) * 16);
+  dg.reserve(sizeof(double) * 16);
+  de.reserve(sizeof(double));
+  de_gamma_kernel<<<1, 32, 0, ctx->stream>>>(a, du.as<double>(), dg.as<double>(), de.as<double>());
+  ctx->launches++;
+  ATTN_CHECK_CUDA(cudaGetLastError());
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(gamma16, dg.p, sizeof(double) * 16, cudaMemcpyDeviceToHost, ctx->stream));
+  ATTN_CHECK_CUDA(cudaMemcpyAsync(e_k, de.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+double attn_state::de_update(const std::vector<int>* only) {
+  const int nDE = (int)des.size();
+  if (!nDE) return 0.0;
+  std::vector<int> sel;
+  if (only) sel = *only;
+  else for (int k = 0; k < nDE; ++k) sel.push_back(k);
+  const int nS = (int)sel.size();
+  if (!nS) return 0.0;
+  const bool all = (nS == nDE);
+  DESetup S;
+  de_setup(sel, S);
+  DEDev d;
+  probe_expectations(S.F, S.P, d.vals);
+  DEArgs a = de_upload(ctx, S, d);
+  DevBuf d_uin, d_uout, d_e;
+  std::vector<double> uin(16L * nS);
+  for (int q = 0; q < nS; ++q) std::copy(us[sel[q]].begin(), us[sel[q]].end(), uin.begin() + 16L * q);
   upload(ctx, d_uin, uin.data(), sizeof(double) * uin.size());
   d_uout.reserve(sizeof(double) * uin.size());
-  d_e.reserve(sizeof(double) * 2 * nDE);
-  // reduced density matrices on the disentangler sites (recorded at the first update)
+  d_e.reserve(sizeof(double) * 2 * nS);
+  // reduced density matrices on the disentangler sites (recorded at the first full update)
+  const bool first = all && !first_de_done;
   std::vector<double> rho_h;
-  if (!first_de_done || rho_out) {
-    std::vector<double> pv(P.size());
-    ATTN_CHECK_CUDA(cudaMemcpyAsync(pv.data(), vals.p, sizeof(double) * pv.size(), cudaMemcpyDeviceToHost, ctx->stream));
-    ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
-    rho_h.assign(16L * nDE, 0.0);
-    for (long q = 0; q < 16L * nDE; ++q) rho_h[q] = pv[rho_idx[q]];
-    if (rho_out) *rho_out = rho_h;
-  }
-  const bool first = !first_de_done;
   if (first) {
+    std::vector<double> pv(S.P.size());
+    ATTN_CHECK_CUDA(cudaMemcpyAsync(pv.data(), d.vals.p, sizeof(double) * pv.size(), cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+    ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+    rho_h.assign(16L * nS, 0.0);
+    for (long q = 0; q < 16L * nS; ++q) rho_h[q] = pv[S.rho_idx[q]];
     rho_first = rho_h;
     first_de_done = true;
   }
-  DEArgs a;
-  a.n_de = nDE;
-  a.ent_begin = d_eb.as<int>();
-  a.ent_midx = d_em.as<int>();
-  a.ent_C = d_ec.as<double>();
-  a.lambda = d_lam.as<double>();
-  a.rho_idx = d_rho.as<int>();
-  a.vals = vals.as<double>();
   a.u_in = d_uin.as<double>();
   a.u_out = d_uout.as<double>();
   a.e_out = d_e.as<double>();
-  a.max_iter = ctx->cfg.de_max_iter;
-  a.rel_dev = ctx->cfg.de_rel_dev;
   if (first && learned) {
     // learned start: keep the prediction where it is finite and does not raise E_k
-    std::vector<double> up(16L * nDE);
-    learned->net.predict(nDE, rho_h.data(), up.data());
+    std::vector<double> up(16L * nS);
+    learned->net.predict(nS, rho_h.data(), up.data());
     DevBuf d_up, d_ep, d_e0;
     upload(ctx, d_up, up.data(), sizeof(double) * up.size());
-    d_ep.reserve(sizeof(double) * nDE);
-    d_e0.reserve(sizeof(double) * nDE);
-    de_energy_kernel<<<(nDE + 63) / 64, 64, 0, ctx->stream>>>(a, d_up.as<double>(), d_ep.as<double>());
-    de_energy_kernel<<<(nDE + 63) / 64, 64, 0, ctx->stream>>>(a, d_uin.as<double>(), d_e0.as<double>());
+    d_ep.reserve(sizeof(double) * nS);
+    d_e0.reserve(sizeof(double) * nS);
+    de_energy_kernel<<<(nS + 63) / 64, 64, 0, ctx->stream>>>(a, d_up.as<double>(), d_ep.as<double>());
+    de_energy_kernel<<<(nS + 63) / 64, 64, 0, ctx->stream>>>(a, d_uin.as<double>(), d_e0.as<double>());
     ctx->launches += 2;
-    std::vector<double> ep(nDE), e0(nDE);
-    ATTN_CHECK_CUDA(cudaMemcpyAsync(ep.data(), d_ep.p, sizeof(double) * nDE, cudaMemcpyDeviceToHost, ctx->stream));
-    ATTN_CHECK_CUDA(cudaMemcpyAsync(e0.data(), d_e0.p, sizeof(double) * nDE, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<double> ep(nS), e0(nS);
+    ATTN_CHECK_CUDA(cudaMemcpyAsync(ep.data(), d_ep.p, sizeof(double) * nS, cudaMemcpyDeviceToHost, ctx->stream));
+    ATTN_CHECK_CUDA(cudaMemcpyAsync(e0.data(), d_e0.p, sizeof(double) * nS, cudaMemcpyDeviceToHost, ctx->stream));
     ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
     learned_used = learned_fallback = 0;
-    for (int k = 0; k < nDE; ++k) {
-      bool ok = std::isfinite(ep[k]);
-      for (int i = 0; i < 16; ++i) ok = ok && std::isfinite(up[16L * k + i]);
-      if (ok && ep[k] <= e0[k]) {
-        std::copy(up.begin() + 16L * k, up.begin() + 16L * k + 16, uin.begin() + 16L * k);
+    for (int q = 0; q < nS; ++q) {
+      bool ok = std::isfinite(ep[q]);
+      for (int i = 0; i < 16; ++i) ok = ok && std::isfinite(up[16L * q + i]);
+      if (ok && ep[q] <= e0[q]) {
+        std::copy(up.begin() + 16L * q, up.begin() + 16L * q + 16, uin.begin() + 16L * q);
         ++learned_used;
       } else {
         ++learned_fallback;
@@ -641,20 +829,23 @@ double attn_state::de_update(const std::vector<std::vector<double>>* u_start, st
     upload(ctx, d_uin, uin.data(), sizeof(double) * uin.size());
     a.u_in = d_uin.as<double>();
   }
-  de_mera_kernel<<<(nDE + 63) / 64, 64, 0, ctx->stream>>>(a);
+  if (ctx->cfg.de_method == 1) de_rgd_kernel<<<(nS + 63) / 64, 64, 0, ctx->stream>>>(a);
+  else de_mera_kernel<<<(nS + 63) / 64, 64, 0, ctx->stream>>>(a);
   ctx->launches++;
   ATTN_CHECK_CUDA(cudaGetLastError());
-  std::vector<double> uout(uin.size()), eo(2L * nDE);
+  std::vector<double> uout(uin.size()), eo(2L * nS);
   ATTN_CHECK_CUDA(cudaMemcpyAsync(uout.data(), d_uout.p, sizeof(double) * uout.size(), cudaMemcpyDeviceToHost, ctx->stream));
   ATTN_CHECK_CUDA(cudaMemcpyAsync(eo.data(), d_e.p, sizeof(double) * eo.size(), cudaMemcpyDeviceToHost, ctx->stream));
   ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  if ((int)last_de_energy.size() != 2 * nDE) last_de_energy.assign(2L * nDE, std::nan(""));
   double dE = 0.0;
-  for (int k = 0; k < nDE; ++k) {
-    ATTN_REQUIRE(std::isfinite(eo[2 * k + 1]), ATTN_ENONFINITE, "non-finite disentangler energy");
-    us[k].assign(uout.begin() + 16L * k, uout.begin() + 16L * k + 16);
-    dE += eo[2 * k + 1] - eo[2 * k];
+  for (int q = 0; q < nS; ++q) {
+    ATTN_REQUIRE(std::isfinite(eo[2 * q + 1]), ATTN_ENONFINITE, "non-finite disentangler energy");
+    us[sel[q]].assign(uout.begin() + 16L * q, uout.begin() + 16L * q + 16);
+    dE += eo[2 * q + 1] - eo[2 * q];
+    last_de_energy[2 * sel[q]] = eo[2 * q];
+    last_de_energy[2 * sel[q] + 1] = eo[2 * q + 1];
   }
-  last_de_energy.assign(eo.begin(), eo.end());
   mapped_ready = false;
   return dE;
 }

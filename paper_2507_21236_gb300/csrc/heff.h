@@ -48,6 +48,7 @@ struct attn_heff {
   bool tc_ready = false;
   void* tc = nullptr;     // opaque, owned by heff_tc.cu
   EigGraph* eg = nullptr; // cached eigensolve graph (use_graphs)
+  attn::DevBuf host_x;    // device copy of the tensor of attn_eigsolve_host
   double flops() const;
   void apply_f64(const double* x, double* y);
   void apply_bf16(const double* x, double* y);

@@ -13,7 +13,8 @@
 //  - Mapping H' = D^T H D per term (Sec. 4.3, Algorithm 1): case (a)/(b) by
 //    embedding the term and u on the union of sites.
 //  - Rank-1 split of each mapped term by successive SVDs (one-sided Jacobi),
-//    at most d^2 = 4 products for a two-site term (Sec. 4.3).
+//    at most d^2 = 4 products for a two-site term (Sec. 4.3); optionally terms on
+//    the same sites are summed first (the compression suggested in Sec. 6.2.2).
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -392,6 +393,23 @@ std::vector<Term> map_terms(const Model& M, const std::vector<std::pair<int, int
     for (int a = 0; a < nt.n; ++a) nt.site[a] = target[a];
     nt.op = res;
     out.push_back(nt);
+  }
+  return out;
+}
+
+std::vector<Term> compress_terms(const std::vector<Term>& terms) {
+  std::map<std::vector<int>, size_t> at;
+  std::vector<Term> out;
+  for (const Term& t : terms) {
+    std::vector<int> key(t.site, t.site + t.n);
+    auto it = at.find(key);
+    if (it == at.end()) {
+      at[key] = out.size();
+      out.push_back(t);
+    } else {
+      std::vector<double>& op = out[it->second].op;
+      for (size_t i = 0; i < op.size(); ++i) op[i] += t.op[i];
+    }
   }
   return out;
 }

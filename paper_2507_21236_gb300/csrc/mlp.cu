@@ -164,7 +164,8 @@ __global__ void sum_kernel(const float* a, int n, float* out) {
   *out = s;
 }
 
-inline int g1(int n) { return (n + 255) / 256; }
+inline int g1(int n) { return (n + 255) / 256; }  // blocks of 256 threads
+inline int g128(int n) { return (n + 127) / 128; }  // blocks of 128 threads
 
 }  // namespace
 
@@ -211,7 +212,7 @@ void Mlp::upload_inputs(int B, const double* rho_host, const double* ut_host) {
 void Mlp::predict(int B, const double* rho_host, double* u_host) {
   upload_inputs(B, rho_host, nullptr);
   forward(B);
-  head_kernel<<<g1(B), 128, 0, ctx->stream>>>(mo.as<float>(), B, u.as<float>(), nullptr, nullptr, nullptr);
+  head_kernel<<<g128(B), 128, 0, ctx->stream>>>(mo.as<float>(), B, u.as<float>(), nullptr, nullptr, nullptr);
   ctx->launches++;
   std::vector<float> hu((size_t)B * 16);
   ATTN_CHECK_CUDA(cudaMemcpyAsync(hu.data(), u.p, sizeof(float) * hu.size(), cudaMemcpyDeviceToHost, ctx->stream));
@@ -225,7 +226,7 @@ float Mlp::loss_grad(int B) {
   float* G = grad.as<float>();
   cudaStream_t s = ctx->stream;
   forward(B);
-  head_kernel<<<g1(B), 128, 0, s>>>(mo.as<float>(), B, u.as<float>(), ut.as<double>(), lp.as<float>(), gm.as<float>());
+  head_kernel<<<g128(B), 128, 0, s>>>(mo.as<float>(), B, u.as<float>(), ut.as<double>(), lp.as<float>(), gm.as<float>());
   sum_kernel<<<1, 1, 0, s>>>(lp.as<float>(), B, lp.as<float>() + B);
   // layer 3
   back_weight_kernel<<<g1(NO * NH), 256, 0, s>>>(gm.as<float>(), h2.as<float>(), G + OFF_W3, G + OFF_B3, B, NH, NO);

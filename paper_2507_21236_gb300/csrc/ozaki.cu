@@ -16,23 +16,29 @@
 //  * the slice pairs (s, t) with s + t <= 7 (21 of 36; the rest lie below
 //    2^-46 of the row scales) are multiplied on the tensor cores. Pairs on
 //    one diagonal c = s + t share the scale 2^(2-8c) and accumulate into one
-//    TMEM accumulator. Every product is an integer below 2^14 in magnitude and
-//    a diagonal has at most 6 pairs, so over one 64-wide K block every partial
-//    sum stays below 6 * 2^14 * 64 < 2^23 and the FP32 accumulation is exact;
-//  * after each K block the epilogue folds the six diagonals into an int64
-//    fixed-point sum per output element (unit 2^-46 of the row scales; the
-//    finest diagonal is rounded to that unit), and converts to FP64 once.
+//    TMEM accumulator. Every product is an integer of magnitude at most 2^14;
+//  * diagonal d sums d + 1 slice pairs, so it can accumulate several K blocks in
+//    TMEM before its partial sums could leave the exact FP32 range: 16, 8, 5, 3,
+//    3 and 2 blocks of 64 for d = 0 .. 5 keep them at or below 2^24. At the end of
+//    each such window the epilogue folds the diagonal into an int64 fixed-point
+//    sum per output element (unit 2^-46 of the row scales; the finest diagonal is
+//    rounded to that unit) while the MMAs of the other diagonals go on, and the
+//    sum is converted to FP64 once.
 //
 // The error is normwise: |C - C~|_ij <= about (K + 2) 2^-46 2^(E_i + E_j),
 // with 2^E_i and 2^E_j at most twice the largest |entry| of row i of P and of
 // row j of Q. K per launch is limited to 65536 so the int64 sum cannot overflow.
 //
 // Kernel: one CTA per 128 x 64 output tile of one batch entry. Warp 0 is the
-// TMA producer, warp 1 allocates TMEM and issues the MMAs, warps 2-17 read the
-// diagonals (four warps per 32-lane quarter w % 4, 16 columns each). The six Q slices
-// of a K block (48 KB) are double-buffered; the P slices stream through a ring
-// of eight 16 KB stages. All waits are bounded; on a timeout the CTA records an
-// error code, stops issuing, drains its copies and frees TMEM.
+// TMA producer; warps 1 and 2 issue the MMAs, each for its own set of diagonals
+// (an MMA costs its issuing thread about as long as the tensor pipe takes for an
+// N = 64 tile, so one thread cannot keep the pipe busy); warps 3-18 read the
+// diagonals (four warps per 32-lane quarter w % 4, 16 columns each). A diagonal is
+// handed back to its issuer as soon as it has been read, so the epilogue of one
+// window overlaps the MMAs of the next. The six Q slices of a K block (48 KB) are
+// double-buffered; the P slices stream through a ring of eight 16 KB stages. All
+// waits are bounded; on a timeout the CTA records an error code, stops issuing,
+// drains its copies and frees TMEM.
 #include <algorithm>
 
 #include "ozaki.h"
@@ -46,7 +52,7 @@ using namespace tc;
 
 constexpr int kSlices = 6;
 constexpr int kDiags = 6;               // c = s + t = 2 .. 7
-constexpr int kOzThreads = 576;         // 2 role warps + 16 epilogue warps
+constexpr int kOzThreads = 608;         // 3 role warps + 16 epilogue warps
 constexpr int kQRows = 64;              // output tile columns (rows of Q)
 constexpr int kPBytes = 128 * 128;      // one 128-row x 64-wide BF16 K block of one P slice
 constexpr int kQBytes = kQRows * 128;   // one 64-row K block of one Q slice
@@ -54,6 +60,13 @@ constexpr int kPStages = 8;
 constexpr int kQBufBytes = kSlices * kQBytes;
 constexpr int kEmptyRow = -2000;        // exponent of an all-zero row
 constexpr int kUnitExp = 46;            // fixed-point unit 2^-46 of the row scales
+// K blocks diagonal d accumulates in TMEM before the epilogue folds it: diagonal d
+// sums d + 1 slice pairs of products below 2^14 in magnitude, so over F_d blocks of
+// 64 its partial sums stay below (d + 1) 2^14 64 F_d <= 2^24 and FP32 holds them
+// exactly (16, 8, 5, 3, 3, 2 blocks for d = 0 .. 5).
+__device__ __constant__ int kFold[kDiags] = {16, 8, 5, 3, 3, 2};
+// The two MMA issuers own complementary diagonal sets (11 and 10 slice pairs).
+constexpr uint32_t kIssuer0Diags = (1u << 0) | (1u << 3) | (1u << 5), kIssuer1Diags = (1u << 1) | (1u << 2) | (1u << 4);
 
 struct OzParams {
   int M, N, nkb;           // rows of P, rows of Q, 64-wide K blocks
@@ -72,6 +85,10 @@ struct OzMaps {
   CUtensorMap p, q;  // [batches * 6][rows][Kpad] BF16, boxes {64, 128, 1} and {64, 64, 1}
 };
 
+__device__ __forceinline__ bool window_end(int d, int kb, int nkb) {
+  return (kb + 1) % kFold[d] == 0 || kb == nkb - 1;
+}
+
 __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_constant__ OzMaps maps, OzParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -82,13 +99,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
   const uint32_t sBar = sP + kPStages * kPBytes;
   enum {
     QFULL = 0,
-    QEMPTY = 2,
+    QEMPTY = 2,                 // both issuers release a Q buffer
     PFULL = 4,
-    PEMPTY = 4 + kPStages,
-    DFULL = 4 + 2 * kPStages,   // the K block's diagonals are complete in TMEM
-    DEMPTY = 5 + 2 * kPStages,  // the epilogue has read them
-    MDONE = 6 + 2 * kPStages,   // every MMA of the CTA has completed
-    NBAR = 7 + 2 * kPStages
+    PEMPTY = 4 + kPStages,      // both issuers release a P stage
+    DFULL = 4 + 2 * kPStages,   // [d]: a window of diagonal d is complete in TMEM
+    DEMPTY = DFULL + kDiags,    // [d]: the epilogue has read it
+    MDONE = DEMPTY + kDiags,    // [issuer]: every MMA of that issuer has completed
+    NBAR = MDONE + 2
   };
   uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + (sBar - base));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBAR);
@@ -104,15 +121,17 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
       mbar_init(bar(QFULL + i), 1);
-      mbar_init(bar(QEMPTY + i), 1);
+      mbar_init(bar(QEMPTY + i), 2);
+      mbar_init(bar(MDONE + i), 1);
     }
     for (int i = 0; i < kPStages; ++i) {
       mbar_init(bar(PFULL + i), 1);
-      mbar_init(bar(PEMPTY + i), 1);
+      mbar_init(bar(PEMPTY + i), 2);
     }
-    mbar_init(bar(DFULL), 1);
-    mbar_init(bar(DEMPTY), 16);
-    mbar_init(bar(MDONE), 1);
+    for (int d = 0; d < kDiags; ++d) {
+      mbar_init(bar(DFULL + d), 1);
+      mbar_init(bar(DEMPTY + d), 16);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -160,8 +179,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
       long long t0 = clock64();
       while (!mbar_try_wait(bar(PFULL + q % kPStages), (q / kPStages) & 1) && clock64() - t0 < kWaitCycles) {}
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issue: diagonal d accumulates the pairs (s, t) with s + t = d (0-based slices)
+  } else if ((warp == 1 || warp == 2) && lane == 0) {
+    // ---- MMA issue, one thread per diagonal set: diagonal d accumulates the pairs
+    // (s, t) with s + t = d (0-based slices) over a window of kFold[d] K blocks
+    const int me = warp - 1;
+    const uint32_t mine = me == 0 ? kIssuer0Diags : kIssuer1Diags;
     const uint32_t id = idesc_bf16(128, kQRows);
     const uint64_t dP0 = sw128_desc(sP), dQ0 = sw128_desc(sQ);
     int pst = 0;
@@ -169,8 +191,6 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
     bool ok = true;
     for (int kb = 0; ok && kb < nkb; ++kb) {
       const int qb = kb & 1;
-      // the diagonals hold the previous K block until the epilogue has read them
-      if (kb > 0 && !mbar_wait(bar(DEMPTY), (kb - 1) & 1, p.err, 63, abort_flag)) break;
       if (!mbar_wait(bar(QFULL + qb), (kb >> 1) & 1, p.err, 64, abort_flag)) break;
       fence_after();
       uint32_t touched = 0;
@@ -180,46 +200,61 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
         const uint64_t dP = dP0 + (uint64_t)(pst * (kPBytes >> 4));
         for (int t = 0; s + t < kDiags; ++t) {
           const int d = s + t;
+          if (!((mine >> d) & 1u)) continue;
+          const bool first = (kb % kFold[d] == 0) && !((touched >> d) & 1u);
+          // a new window reuses the diagonal's accumulator once the epilogue has read the last one
+          if (first && kb > 0 &&
+              !mbar_wait(bar(DEMPTY + d), (kb / kFold[d] - 1) & 1, p.err, 63, abort_flag)) {
+            ok = false;
+            break;
+          }
           const uint64_t dQ = dQ0 + (uint64_t)((qb * kQBufBytes + t * kQBytes) >> 4);
-          mma4_ss(tmem + 64u * (uint32_t)d, dP, dQ, id, (touched >> d) & 1u);
+          mma4_ss(tmem + 64u * (uint32_t)d, dP, dQ, id, first ? 0u : 1u);
           touched |= 1u << d;
         }
         mma_commit(bar(PEMPTY + pst));
         if (++pst == kPStages) { pst = 0; pph ^= 1u; }
+        if (!ok) break;
       }
-      if (!ok) break;
       mma_commit(bar(QEMPTY + qb));
-      mma_commit(bar(DFULL));
+      if (!ok) break;
+      for (int d = 0; d < kDiags; ++d)
+        if (((mine >> d) & 1u) && window_end(d, kb, nkb)) mma_commit(bar(DFULL + d));
     }
-    mma_commit(bar(MDONE));
+    mma_commit(bar(MDONE + me));
     long long t0 = clock64();
-    while (!mbar_try_wait(bar(MDONE), 0) && clock64() - t0 < kWaitCycles) {}
-  } else if (warp >= 2) {
-    // ---- epilogue: lane quarter q4, columns 16 h .. 16 h + 15 of the tile
-    const int q4 = warp & 3, h = (warp - 2) >> 2;
+    while (!mbar_try_wait(bar(MDONE + me), 0) && clock64() - t0 < kWaitCycles) {}
+  } else if (warp >= 3) {
+    // ---- epilogue: lane quarter q4, columns 16 h .. 16 h + 15 of the tile; every
+    // finished window of a diagonal is folded into an int64 fixed-point sum
+    const int q4 = warp & 3, h = (warp - 3) >> 2;
     const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
     long long acc[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) acc[c] = 0;
     bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      // warp-uniform: the TMEM loads below are .sync.aligned
-      if (!__all_sync(0xffffffffu, mbar_wait(bar(DFULL), kb & 1, p.err, 66, abort_flag))) { ok = false; break; }
-      fence_after();
+    for (int kb = 0; ok && kb < nkb; ++kb) {
 #pragma unroll
       for (int d = 0; d < kDiags; ++d) {
+        if (!window_end(d, kb, nkb)) continue;
+        // warp-uniform: the TMEM loads below are .sync.aligned
+        if (!__all_sync(0xffffffffu, mbar_wait(bar(DFULL + d), (kb / kFold[d]) & 1, p.err, 66, abort_flag))) {
+          ok = false;
+          break;
+        }
+        fence_after();
         float v[16];
         tmem_ld16(tmem + lane_off + 64u * (uint32_t)d + 16u * (uint32_t)h, v);
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(DEMPTY + d));
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          const long long x = (long long)__float2int_rn(v[c]);  // exact: |v| < 2^23
+          const long long x = (long long)__float2int_rn(v[c]);  // exact: |v| <= 2^24
           if (d < kDiags - 1) acc[c] += x << (8 * (kDiags - 2 - d));
           else acc[c] += (x + 128) >> 8;  // the finest diagonal, rounded to the unit
         }
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar(DEMPTY));
     }
     const int i = m0 + q4 * 32 + lane;
     if (ok && i < p.M) {

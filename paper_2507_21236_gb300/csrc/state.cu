@@ -161,6 +161,7 @@ void attn_state::move_centre(int target) {
 
 void attn_state::set_products() {
   mapped = map_terms(model, des, us);
+  if (ctx->cfg.compress_terms) mapped = compress_terms(mapped);
   prods = split_products(mapped);
   for (auto& e : env) e.valid = false;
   mapped_ready = true;

@@ -35,7 +35,19 @@ struct ProbeFactor {
 };
 struct Probe {
   int n;
-  int f[3];
+  int f[8];
+};
+
+// Probes and coefficient tables of the MERA-like update of a set of disentanglers.
+struct DESetup {
+  std::vector<int> sel;              // disentangler indices, by position
+  std::vector<ProbeFactor> F;
+  std::vector<Probe> P;
+  std::vector<int> rho_idx;          // [pos][16] probe index of each rho_ij entry
+  std::vector<int> ent_begin;        // [pos + 1] entry ranges
+  std::vector<int> ent_midx;         // [entry][16] probe index of each M entry
+  std::vector<double> ent_C;         // [entry][16]
+  std::vector<double> lambda;        // [pos] summed spectral-norm shifts
 };
 
 }  // namespace attn
@@ -83,10 +95,22 @@ struct attn_state {
   // <psi| prod_s f_s |psi> for rank-1 probes of one-site factors (device results)
   void probe_expectations(const std::vector<attn::ProbeFactor>& F, const std::vector<attn::Probe>& P,
                           attn::DevBuf& vals);
-  // MERA-like update of every disentangler (Sec. 4.1.1); returns sum of dE_k
-  double de_update(const std::vector<std::vector<double>>* u_start, std::vector<double>* rho_out);
+  // MERA-like update of the listed disentanglers (all when `only` is null), Sec. 4.1.1;
+  // returns the sum of their dE_k
+  void de_setup(const std::vector<int>& sel, attn::DESetup& S);
+  double de_update(const std::vector<int>* only);
+  // two-site density matrices of the TTN on the listed disentanglers' sites ([pos][16])
+  std::vector<double> de_rdms(const std::vector<int>& sel);
+  // Gamma_k at u (shifted terms, Eq. contracted) and the true E_k(u)
+  void de_environment(int k, const double* u16, double* gamma16, double* e_k);
+  // <psi_aTTN| o |psi_aTTN> of products of one-site operators (Eq. obs): nsites[o] in
+  // 1..4, sites[4 o ..], ops[16 o ..] (2 x 2 row-major per site); mapped through the
+  // disentanglers an observable spans at most eight sites
+  std::vector<double> measure(int n_obs, const int* nsites, const int* sites, const double* ops);
   attn_heff* build_heff(int n);
   double energy();
   double local_step(int n);
   double isometry_error();
+  void save(const char* path);
+  void load(const char* path);
 };

@@ -133,3 +133,59 @@ def test_graph_cache_rebuilt_after_scratch_reallocation():
     for (t0, v0), (t1, v1) in zip(results[0], results[1]):
         assert abs(t0 - t1) <= 1e-13 * abs(t0)
         assert np.abs(v0 - v1).max() <= 1e-12
+
+
+def test_attn_below_ttn_at_equal_bond_dimension():
+    """8x8 TFIM near the critical field (h = 3.04), m = 16, eight sweeps from the same
+    tensors: the aTTN (disentanglers placed by the paper's rule, S_TTN = 1) ends at or
+    below the plain TTN's energy (the augmented ansatz contains the TTN), and both
+    runs are variational and monotone sweep to sweep."""
+    L, m, sweeps = 8, 16, 8
+    tree = Tree(L * L, m)
+    raw = raw_tree_tensors(tree.shape, 3)
+    out = {}
+    for n_de in (0, 16):
+        attn, ctx = lib_and_ctx()
+        mod = attn.attn_model_tfim(ctx, L, 3.04)
+        st = attn.attn_state_create(ctx, mod, m, raw)
+        placed = attn.attn_de_place(st, n_de)
+        assert (placed > 0) == (n_de > 0)
+        es = [attn.attn_sweep(st) for _ in range(sweeps)]
+        assert all(b <= a + 1e-9 * abs(a) for a, b in zip(es[:-1], es[1:]))
+        out[n_de] = es
+        attn.attn_state_destroy(st)
+        attn.attn_model_destroy(mod)
+        attn.attn_destroy(ctx)
+    # the first sweep is TTN-only in both runs (S_TTN = 1): identical arithmetic
+    assert out[0][0] == out[16][0]
+    print(f"E/site after {sweeps} sweeps: TTN {out[0][-1] / 64:.10f}, aTTN {out[16][-1] / 64:.10f}")
+    assert out[16][-1] <= out[0][-1]
+
+
+def test_riemannian_de_update_matches_oracle():
+    """de_method 1 (Sec. 4.1.2): Riemannian conjugate gradients on the GPU follow the
+    oracle's iteration from the identity to the same E_k (1e-10) and u (1e-6), and
+    stop at the MERA-like update's energy within 1e-8."""
+    from oracle.de_update import optimise_de_riemannian
+
+    attn, ctx, mod, st, ost, terms, tree, des = _pair(4, 8, 4)
+    cfg = attn.attn_get_config(ctx)
+    cfg.de_method = 1
+    attn.attn_set_config(ctx, cfg)
+    attn.attn_map_hamiltonian(st)
+    attn.attn_ttn_sweep(st)
+    ost.set_products(products_of(terms))
+    ttn_sweep(ost)
+    attn.attn_de_update(st)
+    en = attn.attn_de_energies(st, len(des))
+    for k, p in enumerate(build_problems(ost, terms, des)):
+        u_ref, hist = optimise_de_riemannian(p, np.eye(4))
+        assert abs(en[k, 0] - hist[0]) <= 1e-12 * abs(hist[0])
+        assert abs(en[k, 1] - hist[-1]) <= 1e-10 * abs(hist[-1]), k
+        u = attn.attn_de_get(st, k)
+        assert np.abs(u.T @ u - np.eye(4)).max() < 1e-12
+        assert np.abs(u - u_ref).max() < 1e-6, k
+        assert abs(hist[-1] - optimise_de(p, np.eye(4))[1][-1]) <= 1e-8 * abs(hist[-1])
+    attn.attn_state_destroy(st)
+    attn.attn_model_destroy(mod)
+    attn.attn_destroy(ctx)

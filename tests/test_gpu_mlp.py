@@ -32,7 +32,8 @@ def _batch(rng, B):
     return x, ut
 
 
-def test_forward_loss_and_gradients_match_oracle():
+@pytest.mark.parametrize("B", [24, 300])  # 300: more samples than one block of the head kernel
+def test_forward_loss_and_gradients_match_oracle(B):
     attn, ctx = lib_and_ctx()
     assert attn.attn_mlp_param_count() == 16 * 128 + 128 + 128 * 128 + 128 + 128 * 16 + 16
     rng = np.random.default_rng(0)
@@ -41,7 +42,7 @@ def test_forward_loss_and_gradients_match_oracle():
         p[k] = p[k] + 0.05 * rng.normal(size=p[k].shape)
     pf = _flat(p)
     p32 = _unflat(pf)  # the oracle sees the same (FP32-rounded) parameters
-    x, ut = _batch(rng, 24)
+    x, ut = _batch(rng, B)
     m = attn.attn_mlp_create(ctx, pf)
     u = attn.attn_mlp_predict(m, x)
     u_ref, _ = omlp.forward(p32, x)

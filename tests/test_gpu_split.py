@@ -154,3 +154,30 @@ def test_split_sweep_energy_matches_fp64_fma():
     torch.cuda.synchronize()
     for a, b in zip(*es):
         assert abs(a - b) <= 1e-10 * abs(b), (a, b)
+
+
+def test_split_gemm_exact_at_the_accumulation_bound():
+    """Every entry 126 (2^40 + 2^32 + 2^24 + 2^16 + 2^8 + 1) 2^-47 has all six slice
+    digits equal to 126, so every slice product is 126^2 = 15876 and each diagonal's
+    partial sums reach 97 % of 2^24 within its accumulation window (diagonal 0:
+    15876 x 1024 over K = 1024). The contraction y[i] = sum_j A[i][j] x[j] of one
+    pair product (B = identity) must then equal the scheme's exact fixed-point
+    result bit for bit: diagonals d = 0..4 contribute (d + 1) 15876 K at weight
+    2^(8 (4 - d)) units, the finest one (6 15876 K) / 256 units (an integer here),
+    one unit being 2^-46. A tensor-core accumulator that lost a bit near 2^24
+    would move the top diagonals' sums by whole units at weight up to 2^32."""
+    m0, m1, m2 = 1024, 8, 8
+    F = 126 * sum(1 << (8 * k) for k in range(6))
+    v = F * 2.0 ** -47
+    assert F < 2 ** 47 and v == F / 2 ** 47
+    A = np.full((1, m0, m0), v)
+    B = np.eye(m1)[None]
+    x = np.full((m0, m1, m2), v)
+    attn, ctx = lib_and_ctx({"f64_split": 1})
+    y = _apply(attn, ctx, (m0, m1, m2), (None, None, None), {0: (A, B)}, None, x, attn.ATTN_F64)
+    K = m0
+    acc = sum((d + 1) * 15876 * K << (8 * (4 - d)) for d in range(5)) + (6 * 15876 * K) // 256
+    assert (6 * 15876 * K) % 256 == 0
+    expected = float(acc) * 2.0 ** -46
+    assert np.all(y == expected), (float(y.min()), float(y.max()), expected)
+    attn.attn_destroy(ctx)
