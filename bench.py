@@ -376,7 +376,9 @@ def precision_arms(attn):
     k3 = {"matvec_dtype": attn.ATTN_BF16, "refine_steps": 3, "refine_inner": 16}
     jd = {"matvec_dtype": attn.ATTN_BF16, "refine_steps": 8, "refine_inner": 16, "refine_tol": 1e-10}
     # *_split: FP64 contractions as exact BF16 slice products on the tensor cores
+    tf = dict(jd, matvec_dtype=attn.ATTN_TF32)
     return {"f64": {}, "mixed_k3": k3, "mixed": jd, "f64_split": {"f64_split": 1},
+            "mixed_tf32_split": dict(tf, f64_split=1),
             "mixed_k3_split": dict(k3, f64_split=1), "mixed_split": dict(jd, f64_split=1),
             "mixed_split_t12": dict(jd, f64_split=1, refine_tol=1e-12)}
 
@@ -638,6 +640,93 @@ def run_sttn(args):
           flush=True)
 
 
+def train_learned_start(attn, ctx, torch):
+    """MLP of the learned disentangler start, trained on the (two-site density matrix at
+    the first update, final disentangler) pairs of plain 8x8 (seeds 0-3) and 16x16
+    (seeds 0-1) TFIM runs at m = 16 (three aTTN sweeps each)."""
+    from inputs import raw_tree_tensors
+    from oracle.mlp import init_params
+
+    rhos, targets = [], []
+    for Ls, seeds in ((8, range(4)), (16, range(2))):
+        for seed in seeds:
+            model = attn.attn_model_tfim(ctx, Ls, H_FIELD)
+            st = attn.attn_state_create(ctx, model, 16, raw_tree_tensors(tree_shapes(Ls * Ls, 16), seed))
+            n = attn.attn_de_place(st, Ls * Ls // 4)
+            for _ in range(3):
+                attn.attn_sweep(st)
+            r, u = attn.attn_de_training_pairs(st, n)
+            rhos.append(r)
+            targets.append(u)
+            attn.attn_state_destroy(st)
+            attn.attn_model_destroy(model)
+    p = init_params(0)
+    flat = np.concatenate([p[k].reshape(-1) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]).astype(np.float32)
+    mlp = attn.attn_mlp_create(ctx, flat)
+    rho, ut = np.concatenate(rhos), np.concatenate(targets)
+    l0, _ = attn.attn_mlp_loss_grad(mlp, rho, ut)
+    l1 = attn.attn_mlp_train(mlp, rho, ut, 600, 2e-3)
+    return mlp, {"samples": int(rho.shape[0]), "loss_before": l0, "loss_after": l1}
+
+
+def run_target(args):
+    """The 32x32 TFIM aTTN at m = 128 (h = 3.04, 184 placed disentanglers), from one set
+    of raw tensors: the FP64 path (contractions as split BF16 products), the mixed path
+    (BF16 Lanczos + FP64 refinement, split contractions), and the mixed path with the
+    learned disentangler start. Per sweep: wall time, energy per site, its change, and
+    the mixed arms' difference to FP64."""
+    import torch
+    from __graft_entry__ import build
+    from inputs import raw_tree_tensors
+    from paper_2507_21236_gb300 import attn
+
+    build()
+    Ls, ms = args.sweep_L, args.sweep_m
+    n = Ls * Ls
+    raw = raw_tree_tensors(tree_shapes(n, ms), 0)
+    stream = torch.cuda.current_stream().cuda_stream
+    out = {}
+    arms = args.arms.split(",")
+    for name in arms:
+        learned = name.endswith("+learned")
+        cfg = arm_config(attn, name.replace("+learned", ""))
+        ctx = attn.attn_create(cfg, stream)
+        mlp = None
+        if learned:
+            mlp, out["learned_training"] = train_learned_start(attn, ctx, torch)
+        model = attn.attn_model_tfim(ctx, Ls, H_FIELD)
+        st = attn.attn_state_create(ctx, model, ms, raw)
+        n_de = attn.attn_de_place(st, n // 4)
+        if mlp is not None:
+            attn.attn_set_learned_init(st, mlp)
+        es, ts = [], []
+        for s in range(args.max_sweeps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            es.append(attn.attn_sweep(st) / n)
+            ts.append(time.perf_counter() - t0)
+            print(json.dumps({"arm": name, "sweep": s + 1, "s": ts[-1], "energy_per_site": es[-1]}), flush=True)
+        rec = {"s_per_sweep": ts, "energy_per_site": es, "delta_per_site": [b - a for a, b in zip(es[:-1], es[1:])],
+               "n_de": n_de}
+        if n_de and args.max_sweeps > 1:
+            e_first = attn.attn_de_energies(st, n_de)  # the last update's E_k before/after
+            rec["sum_Ek_last_update"] = [float(e_first[:, 0].sum()), float(e_first[:, 1].sum())]
+        if mlp is not None:
+            rec["learned_used_fallback"] = list(attn.attn_learned_init_report(st))
+            attn.attn_mlp_destroy(mlp)
+        out[name] = rec
+        attn.attn_state_destroy(st)
+        attn.attn_model_destroy(model)
+        attn.attn_destroy(ctx)
+    ref = out.get(arms[0])
+    for name in arms[1:]:
+        out[name]["minus_" + arms[0] + "_per_site"] = [a - b for a, b in zip(out[name]["energy_per_site"],
+                                                                              ref["energy_per_site"])]
+    print(json.dumps({"metric": "aTTN sweeps, 32x32 TFIM m=128: time per sweep and energy per site by arm",
+                      "config": {"workload": f"tfim{Ls}x{Ls}_m{ms}_target", "L": Ls, "m": ms, "h": H_FIELD,
+                                 "s_ttn": 1, "arms": arms}, "runs": out}), flush=True)
+
+
 # (name, model, L, m, coupling): the matvec benchmark shapes of every configuration
 NODE_CONFIGS = [("C2", "tfim", 8, 32, 3.04), ("C3", "tfim", 16, 64, 3.04), ("C3", "tfim", 16, 128, 3.04),
                 ("C4", "heis", 16, 64, 1.0), ("C4", "heis", 16, 128, 1.0), ("C5", "tfim", 32, 128, 3.04)]
@@ -720,15 +809,25 @@ def run_nodes(args):
                 H = attn.attn_heff_create(ctx, (m, m, m), hint, pairs, trip)
                 fl = attn.attn_heff_info(H)[2]
                 ms = timed_apply(H, x, y, attn.ATTN_BF16, 5)
-                by_counts[key] = (fl, ms, H)
-            fl, ms, _ = by_counts[key]
-            rows.append({"node": i, "counts": list(c[:4]), "gflop": fl / 1e9, "bf16_ms": ms})
+                ms_tf = timed_apply(H, x, y, attn.ATTN_TF32, 5)
+                by_counts[key] = (fl, ms, H, ms_tf)
+            fl, ms, _, ms_tf = by_counts[key]
+            rows.append({"node": i, "counts": list(c[:4]), "gflop": fl / 1e9, "bf16_ms": ms, "tf32_ms": ms_tf})
         # FP64 on a sample: the lightest, the median and the heaviest node
         srt = sorted(rows, key=lambda r: r["gflop"])
         sample = [srt[0], srt[len(srt) // 2], srt[-1]]
         for r in sample:
             H = by_counts[tuple(r["counts"])][2]
             r["f64_ms"] = timed_apply(H, x, y, attn.ATTN_F64, 1)
+        # error of each low precision against FP64 on the heaviest node (normwise, max-abs)
+        H = by_counts[tuple(srt[-1]["counts"])][2]
+        y64 = torch.empty_like(x)
+        attn.attn_heff_apply(H, x.data_ptr(), y64.data_ptr(), attn.ATTN_F64)
+        errs = {}
+        for name, dt in (("bf16", attn.ATTN_BF16), ("tf32", attn.ATTN_TF32)):
+            attn.attn_heff_apply(H, x.data_ptr(), y.data_ptr(), dt)
+            torch.cuda.synchronize()
+            errs[name] = float((y - y64).abs().max() / y64.abs().max())
         # the same FP64 applications with the contractions as exact BF16 slice products
         cfg = attn.attn_get_config(ctx)
         cfg.f64_split = 1
@@ -738,7 +837,7 @@ def run_nodes(args):
             r["f64_split_ms"] = timed_apply(H, x, y, attn.ATTN_F64, 3)
         cfg.f64_split = 0
         attn.attn_set_config(ctx, cfg)
-        for _, _, H in by_counts.values():
+        for _, _, H, _ in by_counts.values():
             attn.attn_heff_destroy(H)
         del pool
         tot_fl = sum(r["gflop"] for r in rows)
@@ -749,7 +848,12 @@ def run_nodes(args):
                     "products_per_node": [min(sum(r["counts"]) for r in rows), max(sum(r["counts"]) for r in rows)],
                     "gflop_per_matvec": [round(srt[0]["gflop"], 2), round(srt[-1]["gflop"], 2)],
                     "bf16": {"ms_all_nodes": round(tot_bf, 3), "tflops_flop_weighted": tot_fl / tot_bf,
-                             "tflops_top": rows[-1]["gflop"] / rows[-1]["bf16_ms"]},
+                             "tflops_top": rows[-1]["gflop"] / rows[-1]["bf16_ms"],
+                             "max_rel_err_vs_f64_heaviest": errs["bf16"]},
+                    "tf32": {"ms_all_nodes": round(sum(r["tf32_ms"] for r in rows), 3),
+                             "tflops_flop_weighted": tot_fl / sum(r["tf32_ms"] for r in rows),
+                             "tflops_top": rows[-1]["gflop"] / rows[-1]["tf32_ms"],
+                             "max_rel_err_vs_f64_heaviest": errs["tf32"]},
                     "f64_sample": {"nodes": [r["node"] for r in sample],
                                    "ms": [round(r["f64_ms"], 3) for r in sample],
                                    "tflops_flop_weighted": f64_fl / f64_ms,
@@ -757,7 +861,7 @@ def run_nodes(args):
                                    "split_tflops_flop_weighted": f64_fl / sum(r["f64_split_ms"] for r in sample)},
                     "bf16_speedup_on_sample": f64_ms / sum(r["bf16_ms"] for r in sample)})
         print(json.dumps(out[-1]), flush=True)
-    print(json.dumps({"metric": "H_eff apply per [m,m,m] node, BF16 tensor cores vs FP64",
+    print(json.dumps({"metric": "H_eff apply per [m,m,m] node, BF16 and TF32 tensor cores vs FP64",
                       "unit": "TFLOP/s", "configs": out}), flush=True)
     attn.attn_destroy(ctx)
 
@@ -765,7 +869,7 @@ def run_nodes(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--mode", default="matvec",
-                    choices=["matvec", "sweep", "nodes", "converge", "split", "sttn", "oracle_sample"])
+                    choices=["matvec", "sweep", "nodes", "converge", "split", "sttn", "target", "oracle_sample"])
     ap.add_argument("--sweep-L", type=int, default=16)
     ap.add_argument("--sweep-m", type=int, default=32)
     ap.add_argument("--max-sweeps", type=int, default=30)
@@ -803,6 +907,8 @@ def main():
         return run_split(args)
     if args.mode == "sttn":
         return run_sttn(args)
+    if args.mode == "target":
+        return run_target(args)
     args.warmup = max(args.warmup, 3)
 
     import torch

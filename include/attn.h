@@ -61,9 +61,9 @@ typedef enum {
 } attn_status;
 
 typedef enum {
-  ATTN_F64 = 0,  /* FP64 CUDA-core contractions */
+  ATTN_F64 = 0,  /* FP64 contractions (CUDA cores, or exact BF16 slice products with f64_split) */
   ATTN_F32 = 1,  /* reserved */
-  ATTN_TF32 = 2, /* reserved */
+  ATTN_TF32 = 2, /* TF32 operands (FP32 rounded to 10 mantissa bits), FP32 accumulation on the tcgen05 tensor cores */
   ATTN_BF16 = 3  /* BF16 operands, FP32 accumulation on the tcgen05 tensor cores */
 } attn_dtype;
 
@@ -80,7 +80,8 @@ typedef struct {
   int de_max_iter;          /* MERA-like update iterations, Sec. 4.1.1 (20) */
   double de_rel_dev;        /* relative energy change that stops them (1e-12) */
   int s_ttn;                /* sweeps without disentangler optimisation, Sec. 6.3 (1) */
-  attn_dtype matvec_dtype;  /* precision of the H_eff contractions in Lanczos (ATTN_F64) */
+  attn_dtype matvec_dtype;  /* precision of the H_eff contractions in Lanczos: ATTN_F64, ATTN_TF32 or ATTN_BF16;
+                               nodes with a link the tensor-core tiles cannot take use FP64 (ATTN_F64) */
   int refine_steps;         /* FP64 corrections (one FP64 matvec each) after a low-precision Lanczos (3) */
   double refine_tol;        /* stop refining when ||H v - theta v|| < tol |theta| or a correction
                                lowers theta by at most tol |theta| (1e-10) */
@@ -292,9 +293,11 @@ ATTN_API attn_status attn_heff_destroy(attn_heff* h);
 /* Counts: n_pair[3], n_triple, and the algorithmic FLOPs of one apply. */
 ATTN_API attn_status attn_heff_info(attn_heff* h, int n_pair[3], int* n_triple, double* flops);
 /* y_dev = H_eff x_dev (both DEVICE FP64 [m0][m1][m2], distinct buffers),
- * contractions in `dtype` (ATTN_F64 or ATTN_BF16 with FP32 accumulation; ATTN_F64
- * runs its larger contractions as exact BF16 slice products when the context's
- * f64_split is set). Asynchronous on the context stream. */
+ * contractions in `dtype`: ATTN_F64 (its larger contractions as exact BF16 slice
+ * products when the context's f64_split is set), or ATTN_BF16 / ATTN_TF32 operands
+ * with FP32 accumulation on the tensor cores, which need every link dimension in
+ * {16, 32, ..., 128} (ATTN_EUNSUPPORTED otherwise). Asynchronous on the context
+ * stream. */
 ATTN_API attn_status attn_heff_apply(attn_heff* h, const double* x_dev, double* y_dev, attn_dtype dtype);
 /* Same with host buffers: copies x in, applies, copies y out (synchronous). */
 ATTN_API attn_status attn_heff_apply_host(attn_heff* h, const double* x_host, double* y_host, attn_dtype dtype);

@@ -115,9 +115,9 @@ struct attn_ctx {
     double flops;
   };
   std::vector<GraphEv>* capture_events = nullptr;
-  // Product split chosen for the tensor-core H_eff, by shape and products per kind
-  // (m0, m1, m2, R0, R1, R2): sweeps rebuild H_eff at every local step.
-  std::map<std::array<int, 6>, int> tc_split_cache;
+  // Product split chosen for the tensor-core H_eff, by shape, products per kind and
+  // operand type (m0, m1, m2, R0, R1, R2, tf32): sweeps rebuild H_eff at every local step.
+  std::map<std::array<int, 7>, int> tc_split_cache;
   void prof_begin(int kid);
   void prof_end(int kid, double flops);
   ~attn_ctx();

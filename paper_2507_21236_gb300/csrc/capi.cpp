@@ -218,8 +218,8 @@ ATTN_API attn_status attn_set_config(attn_ctx* ctx, const attn_config* cfg) {
   NEED(ctx, "ctx");
   NEED(cfg, "cfg");
   ATTN_REQUIRE(cfg->lanczos_depth >= 1 && cfg->lanczos_depth <= 60, ATTN_EINVAL, "lanczos_depth must be 1..60");
-  ATTN_REQUIRE(cfg->matvec_dtype == ATTN_F64 || cfg->matvec_dtype == ATTN_BF16, ATTN_EUNSUPPORTED,
-               "matvec_dtype must be ATTN_F64 or ATTN_BF16");
+  ATTN_REQUIRE(cfg->matvec_dtype == ATTN_F64 || cfg->matvec_dtype == ATTN_BF16 || cfg->matvec_dtype == ATTN_TF32,
+               ATTN_EUNSUPPORTED, "matvec_dtype must be ATTN_F64, ATTN_TF32 or ATTN_BF16");
   ATTN_REQUIRE(cfg->wait_limit_log2 >= 0 && cfg->wait_limit_log2 <= 62, ATTN_EINVAL, "wait_limit_log2 must be 0..62");
   ATTN_REQUIRE(cfg->de_method == 0 || cfg->de_method == 1, ATTN_EINVAL, "de_method must be 0 or 1");
   ctx->cfg = *cfg;
@@ -616,9 +616,9 @@ ATTN_API attn_status attn_heff_apply(attn_heff* h, const double* x, double* y, a
   NEED(x, "x_dev");
   NEED(y, "y_dev");
   ATTN_REQUIRE(x != y, ATTN_EINVAL, "x and y must be distinct buffers");
-  if (dtype == ATTN_F64) h->apply_f64(x, y);
-  else if (dtype == ATTN_BF16) h->apply_bf16(x, y);
-  else throw Error{ATTN_EUNSUPPORTED, "dtype must be ATTN_F64 or ATTN_BF16"};
+  ATTN_REQUIRE(dtype == ATTN_F64 || dtype == ATTN_BF16 || dtype == ATTN_TF32, ATTN_EUNSUPPORTED,
+               "dtype must be ATTN_F64, ATTN_TF32 or ATTN_BF16");
+  h->apply(x, y, dtype);
   ATTN_CATCH
 }
 
@@ -632,9 +632,9 @@ ATTN_API attn_status attn_heff_apply_host(attn_heff* h, const double* xh, double
   double* xd = ctx->ws[2].as<double>();
   double* yd = xd + h->V;
   ATTN_CHECK_CUDA(cudaMemcpyAsync(xd, xh, sizeof(double) * h->V, cudaMemcpyHostToDevice, ctx->stream));
-  if (dtype == ATTN_F64) h->apply_f64(xd, yd);
-  else if (dtype == ATTN_BF16) h->apply_bf16(xd, yd);
-  else throw Error{ATTN_EUNSUPPORTED, "dtype must be ATTN_F64 or ATTN_BF16"};
+  ATTN_REQUIRE(dtype == ATTN_F64 || dtype == ATTN_BF16 || dtype == ATTN_TF32, ATTN_EUNSUPPORTED,
+               "dtype must be ATTN_F64, ATTN_TF32 or ATTN_BF16");
+  h->apply(xd, yd, dtype);
   ATTN_CHECK_CUDA(cudaMemcpyAsync(yh, yd, sizeof(double) * h->V, cudaMemcpyDeviceToHost, ctx->stream));
   ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
   ATTN_CATCH
@@ -647,10 +647,8 @@ static void eigsolve_dev(attn_heff* h, double* T_dev, double* theta, int* iters)
   attn_ctx* ctx = h->ctx;
   const attn_config& cfg = ctx->cfg;
   // shapes the tensor-core tiles cannot take run their matvecs in FP64 (on the GPU)
-  const attn_dtype dt = (cfg.matvec_dtype == ATTN_BF16 && tc_supported(h)) ? ATTN_BF16 : ATTN_F64;
-  MatVec lo = [&](const double* a, double* b) {
-    if (dt == ATTN_BF16) h->apply_bf16(a, b); else h->apply_f64(a, b);
-  };
+  const attn_dtype dt = (cfg.matvec_dtype != ATTN_F64 && tc_supported(h)) ? cfg.matvec_dtype : ATTN_F64;
+  MatVec lo = [&](const double* a, double* b) { h->apply(a, b, dt); };
   MatVec hi = [&](const double* a, double* b) { h->apply_f64(a, b); };
   const int rsteps = (dt != ATTN_F64) ? cfg.refine_steps : 0;
   if (cfg.use_graphs) {

@@ -1,4 +1,4 @@
-// Batched BF16 tensor-core GEMM C = alpha A B^T (both K-major), internal.
+// Batched tensor-core GEMM C = alpha A B^T (both K-major, BF16 or TF32 operands), internal.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -7,10 +7,12 @@
 
 namespace attn {
 
-// A K-major BF16 operand viewed as [batches][rows][K] with row stride ld and
-// batch stride bstride (elements; both multiples of 8, base 16-byte aligned).
+// A K-major operand viewed as [batches][rows][K] with row stride ld and batch stride
+// bstride (elements; 16-byte multiples, base 16-byte aligned): BF16, or FP32 values
+// rounded to TF32 when tf is set.
 struct TnOperand {
-  const __nv_bfloat16* p = nullptr;
+  const void* p = nullptr;
+  bool tf = false;
   int K = 0, rows = 0, batches = 1;
   long ld = 0, bstride = 0;
 };
@@ -21,7 +23,7 @@ struct TnParams {
   int a_bhi = 0, a_blo = 0;             // batch coordinate of A = bhi * a_bhi + blo * a_blo
   int b_bhi = 0, b_blo = 0;
   void* C = nullptr;
-  int c_type = 0;                       // 0 FP32, 1 BF16, 2 FP64
+  int c_type = 0;                       // 0 FP32, 1 BF16, 2 FP64, 3 FP32 rounded to TF32
   long c_rs = 0, c_cs = 1, c_bhi = 0, c_blo = 0;  // element strides of C
   float alpha = 1.0f;
   int accumulate = 0;                   // C += alpha * AB^T instead of C = ...
@@ -29,6 +31,7 @@ struct TnParams {
   int* err = nullptr;                   // set by the launcher
 };
 
-void tn_gemm_bf16(attn_ctx* ctx, const TnOperand& A, const TnOperand& B, TnParams p, DevBuf& err);
+// A and B must have the same operand type.
+void tn_gemm(attn_ctx* ctx, const TnOperand& A, const TnOperand& B, TnParams p, DevBuf& err);
 
 }  // namespace attn

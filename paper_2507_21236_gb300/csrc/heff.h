@@ -44,14 +44,22 @@ struct attn_heff {
   attn::DevBuf pa[3], pb[3];  // FP64 stacks [n][m_p][m_p], [n][m_q][m_q]
   int ntrip = 0;
   attn::DevBuf tr[3];     // FP64 stacks [n][m_l][m_l]
-  // Low-precision tensor-core copies (built on first BF16 apply).
-  bool tc_ready = false;
-  void* tc = nullptr;     // opaque, owned by heff_tc.cu
+  // Low-precision tensor-core copies, built at the first application in that type:
+  // tc[0] BF16 operands, tc[1] TF32 operands (opaque, owned by heff_tc.cu).
+  void* tc[2] = {nullptr, nullptr};
   EigGraph* eg = nullptr; // cached eigensolve graph (use_graphs)
   attn::DevBuf host_x;    // device copy of the tensor of attn_eigsolve_host
   double flops() const;
   void apply_f64(const double* x, double* y);
   void apply_bf16(const double* x, double* y);
+  void apply_tf32(const double* x, double* y);
+  void apply_tc(const double* x, double* y, bool tf32);
+  // contractions in `dt` (ATTN_F64, ATTN_BF16 or ATTN_TF32)
+  void apply(const double* x, double* y, attn_dtype dt) {
+    if (dt == ATTN_BF16) apply_bf16(x, y);
+    else if (dt == ATTN_TF32) apply_tf32(x, y);
+    else apply_f64(x, y);
+  }
   ~attn_heff();
 };
 

@@ -74,7 +74,8 @@ constexpr int kThreads = 640;         // 4 role warps + 16 conversion/epilogue w
 constexpr int kHalfWarps = 4;         // conversion warps per slice half (one Z-full arrival each)
 constexpr int kTileBytes = 128 * 128 * 2;  // one 128 x 128 BF16 tile (two 64-wide K blocks)
 constexpr int kKBlockBytes = 128 * 128;    // 128 rows x 128 bytes
-constexpr int kStages = 10;                // operator ring depth (K blocks)
+constexpr int kStages = 10;                // operator ring depth (K blocks), BF16
+constexpr int kStagesTF = 6;               // the same for TF32: the two FP32 X slices take twice the room
 constexpr int kStagesPP = 14;              // ring depth when every product brings its own slices
 constexpr uint32_t kTmemCols = 512;
 
@@ -106,9 +107,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // kPP = false: the CTA's two X slices are loaded once and serve every product.
 // kPP = true: product r has its own slices (slice z = r S + s of the X map),
 // streamed through the ring between B_r and A_r.
-template <bool kPP>
+// kTF = false: BF16 operands (kind::f16), the stage-1 result packed to BF16 in TMEM
+// by the conversion warps; kTF = true: TF32 operands (kind::tf32, FP32 storage
+// rounded to TF32), and stage 2 reads the FP32 stage-1 result from TMEM as it is
+// (the MMA uses its TF32 part), so there is no conversion pass.
+template <bool kPP, bool kTF>
 __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_constant__ TcMaps maps, TcParams prm) {
-  constexpr int NS = kPP ? kStagesPP : kStages;
+  constexpr int NS = kPP ? kStagesPP : (kTF ? kStagesTF : kStages);
+  constexpr int KB = kTF ? 32 : 64;  // elements per 128-byte K block
+  constexpr int KS = kTF ? 8 : 16;   // elements per MMA K step (32 bytes)
+  constexpr int kXBytes = (kTF ? 4 : 2) * kTileBytes;  // X of both slices: up to 4 (TF32) or 2 K blocks
   extern __shared__ uint8_t smem_raw[];
   // 1024-aligned regions: X of both slices (K block kb of slice u at
   // 32 KB kb + 16 KB u; absent when kPP), operator ring, barriers.
@@ -116,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
   const uint32_t sX = base;
-  const uint32_t sRing = kPP ? base : base + 2 * kTileBytes;
+  const uint32_t sRing = kPP ? base : base + kXBytes;
   const uint32_t sBar = sRing + NS * kKBlockBytes;
   enum {
     XFULL = 0,
@@ -178,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
   // TMEM: D1 of slice u in columns 128u .. 128u+P-1 (Z^T packed in place), D2 of slice u at 256 + 128u
   auto tD1 = [&](int u) { return tmem + 128u * (uint32_t)u; };
   auto tD2 = [&](int u) { return tmem + 256u + 128u * (uint32_t)u; };
-  const int nkbQ = (Q + 63) / 64, nkbP = (P + 63) / 64;
+  const int nkbQ = (Q + KB - 1) / KB, nkbP = (P + KB - 1) / KB;
   const CUtensorMap* mX = &maps.x[kind];
   const CUtensorMap* mA = &maps.a[kind];
   const CUtensorMap* mB = &maps.b[kind];
@@ -190,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
       mbar_expect_tx(bar(XFULL), (uint32_t)(nsl * nkbQ * P * 128));
       for (int u = 0; u < nsl; ++u)
         for (int kb = 0; kb < nkbQ; ++kb)
-          tma_load_3d(sX + kb * kTileBytes + u * (kTileBytes / 2), mX, 64 * kb, 0, s0 + u, bar(XFULL));
+          tma_load_3d(sX + kb * kTileBytes + u * (kTileBytes / 2), mX, KB * kb, 0, s0 + u, bar(XFULL));
     }
     int issued = 0;
     int st = 0;       // ring stage of the next load
@@ -211,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
             break;
           }
           mbar_expect_tx(bar(FULL + st), bytes);
-          tma_load_3d(sRing + st * kKBlockBytes, mp, 64 * kb, 0, z, bar(FULL + st));
+          tma_load_3d(sRing + st * kKBlockBytes, mp, KB * kb, 0, z, bar(FULL + st));
           ++issued;
           if (++st == NS) { st = 0; ph ^= 1u; }
         }
@@ -231,8 +239,8 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     // single thread cannot issue N = 128 MMAs (64 cycles each) back to back once
     // waits and commits are interleaved. Warp 1 issues stage 1, warp 2 stage 2;
     // the pipe sees S1(r,0), S1(r,1), S2(r,0), S2(r,1), S1(r+1,0), ...
-    const uint32_t id = idesc_bf16(128, P);  // both stages: M = 128 TMEM lanes, N = P
-    const int nk16Q = Q / 16, nk16P = P / 16;
+    const uint32_t id = idesc_of<kTF>(128, P);  // both stages: M = 128 TMEM lanes, N = P
+    const int nk16Q = Q / KS, nk16P = P / KS;   // MMA K steps
     const uint64_t dRing0 = sw128_desc(sRing);  // ring stage st: + st * (kKBlockBytes >> 4)
     const uint32_t barFull = bar(FULL), barEmpty = bar(EMPTY);
     int st = 0;        // ring stage of the product's first K block
@@ -264,10 +272,10 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
                                     : dX0 + (uint64_t)((kb * kTileBytes + u * (kTileBytes / 2)) >> 4);
             const int n4 = nk16Q - 4 * kb;
             if (n4 >= 4) {
-              mma4_ss(tD1(u), dB, dX, id, kb > 0 ? 1u : 0u);
+              mma4_ss_t<kTF>(tD1(u), dB, dX, id, kb > 0 ? 1u : 0u);
             } else {
               for (int k4 = 0; k4 < n4; ++k4)
-                mma_bf16(tD1(u), dB + 2 * k4, dX + 2 * k4, id, (kb > 0 || k4 > 0) ? 1u : 0u);
+                mma_ss<kTF>(tD1(u), dB + 2 * k4, dX + 2 * k4, id, (kb > 0 || k4 > 0) ? 1u : 0u);
             }
             if (u == nsl - 1) mma_commit(barEmpty + 8 * s1);
             if (kPP) mma_commit(barEmpty + 8 * sx);
@@ -291,17 +299,23 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
           int s2 = st;
           uint32_t p2 = ph;
           for (int kb = 0; kb < nkbP; ++kb) {
-            if (!mbar_wait(bar(ZFULL + 2 * u + kb), r & 1, prm.err, 34, abort_flag, prm.wait)) { ok = false; break; }
+            // BF16: each 64-column half of Z^T once the conversion warps packed it;
+            // TF32: the whole stage-1 result once its MMAs are complete
+            if (kTF ? (kb == 0 && !mbar_wait(bar(D1FULL + u), r & 1, prm.err, 34, abort_flag, prm.wait))
+                    : !mbar_wait(bar(ZFULL + 2 * u + kb), r & 1, prm.err, 34, abort_flag, prm.wait)) {
+              ok = false;
+              break;
+            }
             if (u == 0 && !mbar_wait(barFull + 8 * s2, p2, prm.err, 33, abort_flag, prm.wait)) { ok = false; break; }
-            fence_after();  // Z was written by tcgen05.st in other threads
+            fence_after();  // Z was written by tcgen05.st in other threads (BF16) or by MMAs
             const uint64_t dA = dRing0 + (uint64_t)(s2 * (kKBlockBytes >> 4));
-            const uint32_t aZ = tD1(u) + 64u * (uint32_t)kb;
+            const uint32_t aZ = tD1(u) + (kTF ? 32u : 64u) * (uint32_t)kb;
             const int n4 = nk16P - 4 * kb;
             if (n4 >= 4) {
-              mma4_ts(tD2(u), aZ, dA, id, (r > 0 || kb > 0) ? 1u : 0u);
+              mma4_ts_t<kTF>(tD2(u), aZ, dA, id, (r > 0 || kb > 0) ? 1u : 0u);
             } else {
               for (int k4 = 0; k4 < n4; ++k4)
-                mma_bf16_ts(tD2(u), aZ + 8 * k4, dA + 2 * k4, id, (r > 0 || kb > 0 || k4 > 0) ? 1u : 0u);
+                mma_ts<kTF>(tD2(u), aZ + 8 * k4, dA + 2 * k4, id, (r > 0 || kb > 0 || k4 > 0) ? 1u : 0u);
             }
             if (u == nsl - 1) mma_commit(barEmpty + 8 * s2);
             if (++s2 == NS) { s2 = 0; p2 ^= 1u; }
@@ -328,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     const int c0 = 64 * hh;
     const uint32_t tz = tD1(u) + lane_off + (uint32_t)c0;
     bool ok = u < nsl && c0 < P;
-    for (int r = 0; ok && r < R; ++r) {
+    for (int r = 0; !kTF && ok && r < R; ++r) {
       // warp-uniform: the TMEM accesses below are .sync.aligned
       if (!__all_sync(0xffffffffu, mbar_wait(bar(D1FULL + u), r & 1, prm.err, 41, abort_flag, prm.wait))) { ok = false; break; }
       fence_after();
@@ -376,21 +390,26 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
 }
 
 // ------------------------------------------------------------ prep kernels
-// x (fp64 [m0][m1][m2]) -> bf16 slice-major copies for the three pair kinds:
+// Operand element of the tensor-core path: BF16, or FP32 rounded to TF32.
+template <class T> __device__ __forceinline__ T to_operand(double v);
+template <> __device__ __forceinline__ __nv_bfloat16 to_operand<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+template <> __device__ __forceinline__ float to_operand<float>(double v) { return tc::round_tf32(__double2float_rn(v)); }
+
+// x (fp64 [m0][m1][m2]) -> slice-major operand copies for the three pair kinds:
 // X01[c][a][b], X02[b][a][c], X12[a][b][c]. One block handles a 32 x 32 tile of
 // the (b, c) plane of one a: X02 and X12 rows are contiguous in c like x, and
 // the b <-> c transpose for X01 goes through shared memory, so every global
 // access is coalesced.
 constexpr int kTile = 32;
 
-__global__ void prep_x_kernel(const double* __restrict__ x, int m0, int m1, int m2, __nv_bfloat16* x01,
-                              __nv_bfloat16* x02, __nv_bfloat16* x12) {
-  __shared__ __nv_bfloat16 t[kTile][kTile + 2];
+template <class T>
+__global__ void prep_x_kernel(const double* __restrict__ x, int m0, int m1, int m2, T* x01, T* x02, T* x12) {
+  __shared__ T t[kTile][kTile + 2];
   const int a = blockIdx.z, b0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
   for (int bb = threadIdx.y; bb < kTile; bb += blockDim.y) {
     const int b = b0 + bb, c = c0 + threadIdx.x;
     if (b < m1 && c < m2) {
-      const __nv_bfloat16 v = __double2bfloat16(x[((long)a * m1 + b) * m2 + c]);
+      const T v = to_operand<T>(x[((long)a * m1 + b) * m2 + c]);
       t[bb][threadIdx.x] = v;
       if (x02) x02[((long)b * m0 + a) * m2 + c] = v;
       if (x12) x12[((long)a * m1 + b) * m2 + c] = v;
@@ -429,37 +448,43 @@ __global__ void combine_kernel(double* __restrict__ y, int m0, int m1, int m2, c
 
 dim3 tile_grid(const int* m) { return dim3((m[2] + kTile - 1) / kTile, (m[1] + kTile - 1) / kTile, m[0]); }
 
-__global__ void to_bf16_kernel(__nv_bfloat16* dst, const double* src, long n) {
+template <class T>
+__global__ void to_operand_kernel(T* dst, const double* src, long n) {
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
-    dst[e] = __double2bfloat16(src[e]);
+    dst[e] = to_operand<T>(src[e]);
 }
 
-__global__ void identity_bf16_kernel(__nv_bfloat16* dst, int m) {
+template <class T>
+__global__ void identity_operand_kernel(T* dst, int m) {
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)m * m; e += (long)gridDim.x * blockDim.x)
-    dst[e] = __float2bfloat16((e / m == e % m) ? 1.0f : 0.0f);
+    dst[e] = to_operand<T>((e / m == e % m) ? 1.0 : 0.0);
 }
 
 int vgrid(long n) { return (int)std::max<long>(1, std::min<long>((n + 255) / 256, 4096)); }
 
-// Host: 3-D tiled tensor map over a [D2][D1][D0] bf16 array with a {64, rows, 1} box, 128B swizzle.
-void encode_map(CUtensorMap* map, const void* ptr, int d0, int d1, int d2, int box_rows) {
+// Host: 3-D tiled tensor map over a [D2][D1][D0] operand array (BF16, or FP32 holding
+// TF32) with a {128 bytes, rows, 1} box and the 128B swizzle.
+void encode_map(CUtensorMap* map, const void* ptr, int d0, int d1, int d2, int box_rows, bool tf) {
+  const int es = tf ? 4 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
-  cuuint64_t strides[2] = {(cuuint64_t)d0 * 2, (cuuint64_t)d0 * d1 * 2};
-  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)d0 * es, (cuuint64_t)d0 * d1 * es};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult res = tensor_map_encoder()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims,
-                                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult res = tensor_map_encoder()(map, tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                                      const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   ATTN_REQUIRE(res == CUDA_SUCCESS, ATTN_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)res) + ")");
 }
 
 }  // namespace
 
-// Per-H_eff tensor-core state.
+// Per-H_eff tensor-core state of one operand type.
 struct TcState {
-  DevBuf a[3], b[3];     // bf16 operator stacks per kind [R'][P][P], [R'][Q][Q]
+  bool tf = false;       // TF32 operands (FP32 storage) instead of BF16
+  DevBuf a[3], b[3];     // operator stacks per kind [R'][P][P], [R'][Q][Q]
   int R[3] = {0, 0, 0};  // products per kind (incl. internal operators)
-  DevBuf x[3];           // bf16 slice-major input per kind
+  DevBuf x[3];           // slice-major input per kind
   DevBuf y[3];           // fp32 output per kind
   DevBuf err;
   TcMaps maps;
@@ -468,12 +493,13 @@ struct TcState {
   size_t smem = 0;
   int rsplit = 1;        // products of a slice split over this many CTAs (autotuned)
   bool tuned = false;
-  // three-link products: bf16 factors per slot, the slot-2 contraction of one chunk
+  // three-link products: factors per slot, the slot-2 contraction of one chunk
   // of products ([tchunk][m2][m0][m1]) and the per-product kernel's maps and parameters
   int nt = 0, tchunk = 0;
   DevBuf t0, t1, t2, w;
   TcMaps tmaps;
   TcParams tprm;
+  size_t es() const { return tf ? 4 : 2; }
   // Split every kind's product list f ways (at least 8 products per CTA) and lay out
   // the grid: one CTA per slice pair and product range.
   void set_split(int f) {
@@ -501,17 +527,50 @@ bool tc_supported(const attn_heff* h) {
 }
 
 void tc_release(attn_heff* h) {
-  delete static_cast<TcState*>(h->tc);
-  h->tc = nullptr;
-  h->tc_ready = false;
+  for (int i = 0; i < 2; ++i) {
+    delete static_cast<TcState*>(h->tc[i]);
+    h->tc[i] = nullptr;
+  }
 }
 
-static void tc_build(attn_heff* h) {
+namespace {
+
+// Launch the pair-product kernel (or its per-product form) for the state's operand type.
+void launch_sandwich(bool pp, const TcState* t, int grid, const TcMaps& maps, const TcParams& prm, cudaStream_t st) {
+  if (t->tf) {
+    if (pp) sandwich_tc_kernel<true, true><<<grid, kThreads, t->smem, st>>>(maps, prm);
+    else sandwich_tc_kernel<false, true><<<grid, kThreads, t->smem, st>>>(maps, prm);
+  } else {
+    if (pp) sandwich_tc_kernel<true, false><<<grid, kThreads, t->smem, st>>>(maps, prm);
+    else sandwich_tc_kernel<false, false><<<grid, kThreads, t->smem, st>>>(maps, prm);
+  }
+}
+
+template <class T>
+void to_operand(const TcState* t, cudaStream_t st, void* dst, const double* src, long n) {
+  to_operand_kernel<T><<<vgrid(n), 256, 0, st>>>(static_cast<T*>(dst), src, n);
+}
+
+void convert(const TcState* t, cudaStream_t st, void* dst, const double* src, long n) {
+  if (t->tf) to_operand<float>(t, st, dst, src, n);
+  else to_operand<__nv_bfloat16>(t, st, dst, src, n);
+}
+
+void identity(const TcState* t, cudaStream_t st, void* dst, int m) {
+  if (t->tf) identity_operand_kernel<float><<<vgrid((long)m * m), 256, 0, st>>>(static_cast<float*>(dst), m);
+  else identity_operand_kernel<__nv_bfloat16><<<vgrid((long)m * m), 256, 0, st>>>(static_cast<__nv_bfloat16*>(dst), m);
+}
+
+}  // namespace
+
+static TcState* tc_build(attn_heff* h, bool tf) {
   attn_ctx* ctx = h->ctx;
   auto* t = new TcState();
-  h->tc = t;
+  t->tf = tf;
+  h->tc[tf ? 1 : 0] = t;
   cudaStream_t st = ctx->stream;
   const int* m = h->m;
+  const size_t es = t->es();
   int cta = 0, nk = 0;
   for (int k = 0; k < 3; ++k) {
     const int p = kPairP[k], q = kPairQ[k], sl = kPairS[k];
@@ -530,30 +589,30 @@ static void tc_build(attn_heff* h) {
     const int R = h->npair[k] + extra;
     t->R[k] = R;
     if (R == 0) continue;
-    t->a[k].reserve(sizeof(__nv_bfloat16) * (size_t)R * P * P);
-    t->b[k].reserve(sizeof(__nv_bfloat16) * (size_t)R * Q * Q);
-    auto* A = t->a[k].as<__nv_bfloat16>();
-    auto* B = t->b[k].as<__nv_bfloat16>();
+    t->a[k].reserve(es * (size_t)R * P * P);
+    t->b[k].reserve(es * (size_t)R * Q * Q);
+    uint8_t* A = t->a[k].as<uint8_t>();
+    uint8_t* B = t->b[k].as<uint8_t>();
     if (h->npair[k]) {
-      to_bf16_kernel<<<vgrid((long)h->npair[k] * P * P), 256, 0, st>>>(A, h->pa[k].as<double>(), (long)h->npair[k] * P * P);
-      to_bf16_kernel<<<vgrid((long)h->npair[k] * Q * Q), 256, 0, st>>>(B, h->pb[k].as<double>(), (long)h->npair[k] * Q * Q);
+      convert(t, st, A, h->pa[k].as<double>(), (long)h->npair[k] * P * P);
+      convert(t, st, B, h->pb[k].as<double>(), (long)h->npair[k] * Q * Q);
       ctx->launches += 2;
     }
     for (int e = 0; e < extra; ++e) {
-      __nv_bfloat16* Ae = A + (long)(h->npair[k] + e) * P * P;
-      __nv_bfloat16* Be = B + (long)(h->npair[k] + e) * Q * Q;
-      if (ea[e]) to_bf16_kernel<<<vgrid((long)P * P), 256, 0, st>>>(Ae, ea[e], (long)P * P);
-      else identity_bf16_kernel<<<vgrid((long)P * P), 256, 0, st>>>(Ae, P);
-      if (eb[e]) to_bf16_kernel<<<vgrid((long)Q * Q), 256, 0, st>>>(Be, eb[e], (long)Q * Q);
-      else identity_bf16_kernel<<<vgrid((long)Q * Q), 256, 0, st>>>(Be, Q);
+      uint8_t* Ae = A + es * (size_t)(h->npair[k] + e) * P * P;
+      uint8_t* Be = B + es * (size_t)(h->npair[k] + e) * Q * Q;
+      if (ea[e]) convert(t, st, Ae, ea[e], (long)P * P);
+      else identity(t, st, Ae, P);
+      if (eb[e]) convert(t, st, Be, eb[e], (long)Q * Q);
+      else identity(t, st, Be, Q);
       ctx->launches += 2;
     }
     const int S = m[sl];
-    t->x[k].reserve(sizeof(__nv_bfloat16) * (size_t)h->V);
+    t->x[k].reserve(es * (size_t)h->V);
     t->y[k].reserve(sizeof(float) * (size_t)h->V);
-    encode_map(&t->maps.x[nk], t->x[k].p, Q, P, S, P);
-    encode_map(&t->maps.a[nk], t->a[k].p, P, P, R, 128);
-    encode_map(&t->maps.b[nk], t->b[k].p, Q, Q, R, 128);
+    encode_map(&t->maps.x[nk], t->x[k].p, Q, P, S, P, tf);
+    encode_map(&t->maps.a[nk], t->a[k].p, P, P, R, 128, tf);
+    encode_map(&t->maps.b[nk], t->b[k].p, Q, Q, R, 128, tf);
     KindParams& kp = t->prm.kind[nk];
     kp.P = P; kp.Q = Q; kp.S = S; kp.R = R; kp.cta_begin = cta; kp.Y = t->y[k].as<float>();
     kp.rsplit = 1;
@@ -571,21 +630,21 @@ static void tc_build(attn_heff* h) {
     // [c][a][b] and the per-product kernel adds A_r W_r[c] B_r^T onto Y01
     const int nt = h->ntrip, P = m[0], Q = m[1], S = m[2];
     t->nt = nt;
-    t->t0.reserve(sizeof(__nv_bfloat16) * (size_t)nt * P * P);
-    t->t1.reserve(sizeof(__nv_bfloat16) * (size_t)nt * Q * Q);
-    t->t2.reserve(sizeof(__nv_bfloat16) * (size_t)nt * S * S);
-    to_bf16_kernel<<<vgrid((long)nt * P * P), 256, 0, st>>>(t->t0.as<__nv_bfloat16>(), h->tr[0].as<double>(), (long)nt * P * P);
-    to_bf16_kernel<<<vgrid((long)nt * Q * Q), 256, 0, st>>>(t->t1.as<__nv_bfloat16>(), h->tr[1].as<double>(), (long)nt * Q * Q);
-    to_bf16_kernel<<<vgrid((long)nt * S * S), 256, 0, st>>>(t->t2.as<__nv_bfloat16>(), h->tr[2].as<double>(), (long)nt * S * S);
+    t->t0.reserve(es * (size_t)nt * P * P);
+    t->t1.reserve(es * (size_t)nt * Q * Q);
+    t->t2.reserve(es * (size_t)nt * S * S);
+    convert(t, st, t->t0.p, h->tr[0].as<double>(), (long)nt * P * P);
+    convert(t, st, t->t1.p, h->tr[1].as<double>(), (long)nt * Q * Q);
+    convert(t, st, t->t2.p, h->tr[2].as<double>(), (long)nt * S * S);
     ctx->launches += 3;
     // products per chunk: W of one chunk stays under 1 GiB
-    t->tchunk = (int)std::min<long>(nt, std::max<long>(8, (1L << 29) / std::max<long>(h->V, 1)));
-    t->w.reserve(sizeof(__nv_bfloat16) * (size_t)t->tchunk * h->V);
+    t->tchunk = (int)std::min<long>(nt, std::max<long>(8, (1L << 30) / (long)es / std::max<long>(h->V, 1)));
+    t->w.reserve(es * (size_t)t->tchunk * h->V);
     if (!t->R[0]) t->y[0].reserve(sizeof(float) * (size_t)h->V);
-    if (!t->R[2]) t->x[2].reserve(sizeof(__nv_bfloat16) * (size_t)h->V);
-    encode_map(&t->tmaps.x[0], t->w.p, Q, P, t->tchunk * S, P);
-    encode_map(&t->tmaps.a[0], t->t0.p, P, P, nt, 128);
-    encode_map(&t->tmaps.b[0], t->t1.p, Q, Q, nt, 128);
+    if (!t->R[2]) t->x[2].reserve(es * (size_t)h->V);
+    encode_map(&t->tmaps.x[0], t->w.p, Q, P, t->tchunk * S, P, tf);
+    encode_map(&t->tmaps.a[0], t->t0.p, P, P, nt, 128, tf);
+    encode_map(&t->tmaps.b[0], t->t1.p, Q, Q, nt, 128, tf);
     KindParams& kp = t->tprm.kind[0];
     kp.P = P; kp.Q = Q; kp.S = S; kp.R = 0; kp.rsplit = 1; kp.cta_begin = 0;
     kp.Y = t->y[0].as<float>();
@@ -596,21 +655,32 @@ static void tc_build(attn_heff* h) {
   t->smem = 1024 + 2 * (size_t)kTileBytes + (size_t)kStages * kKBlockBytes + 512;
   static_assert(2 * kTileBytes + kStages * kKBlockBytes == kStagesPP * kKBlockBytes,
                 "both kernel modes use the same shared-memory size");
-  ATTN_CHECK_CUDA(cudaFuncSetAttribute(sandwich_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem));
-  ATTN_CHECK_CUDA(cudaFuncSetAttribute(sandwich_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem));
+  static_assert(4 * kTileBytes + kStagesTF * kKBlockBytes == kStagesPP * kKBlockBytes,
+                "the TF32 kernel uses the same shared-memory size");
+  if (tf) {
+    ATTN_CHECK_CUDA(cudaFuncSetAttribute(sandwich_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem));
+    ATTN_CHECK_CUDA(cudaFuncSetAttribute(sandwich_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem));
+  } else {
+    ATTN_CHECK_CUDA(cudaFuncSetAttribute(sandwich_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem));
+    ATTN_CHECK_CUDA(cudaFuncSetAttribute(sandwich_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem));
+  }
   ATTN_CHECK_CUDA(cudaGetLastError());
-  h->tc_ready = true;
+  return t;
 }
 
-// Read and clear the tensor-core error word of an H_eff (0 = ok).
+// Read and clear the tensor-core error words of an H_eff (0 = ok).
 int tc_error(attn_heff* h) {
-  if (!h->tc_ready) return 0;
-  TcState* t = static_cast<TcState*>(h->tc);
-  int e = 0;
-  ATTN_CHECK_CUDA(cudaMemcpyAsync(&e, t->err.p, sizeof(int), cudaMemcpyDeviceToHost, h->ctx->stream));
-  ATTN_CHECK_CUDA(cudaStreamSynchronize(h->ctx->stream));
-  if (e) ATTN_CHECK_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), h->ctx->stream));
-  return e;
+  int out = 0;
+  for (int i = 0; i < 2; ++i) {
+    TcState* t = static_cast<TcState*>(h->tc[i]);
+    if (!t) continue;
+    int e = 0;
+    ATTN_CHECK_CUDA(cudaMemcpyAsync(&e, t->err.p, sizeof(int), cudaMemcpyDeviceToHost, h->ctx->stream));
+    ATTN_CHECK_CUDA(cudaStreamSynchronize(h->ctx->stream));
+    if (e) ATTN_CHECK_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), h->ctx->stream));
+    if (!out) out = e;
+  }
+  return out;
 }
 
 void check_device_errors(attn_ctx* ctx, attn_heff* h) {
@@ -624,25 +694,31 @@ void check_device_errors(attn_ctx* ctx, attn_heff* h) {
 
 using namespace attn;
 
-void attn_heff::apply_bf16(const double* x, double* y) {
+void attn_heff::apply_tc(const double* x, double* y, bool tf) {
   ATTN_REQUIRE(tc_supported(this), ATTN_EUNSUPPORTED,
-               "BF16 tensor-core path needs every link dimension in {16, 32, ..., 128}");
-  if (!tc_ready) tc_build(this);
-  TcState* t = static_cast<TcState*>(tc);
+               "the tensor-core path needs every link dimension in {16, 32, ..., 128}");
+  TcState* t = static_cast<TcState*>(tc[tf ? 1 : 0]);
+  if (!t) t = tc_build(this, tf);
   cudaStream_t st = ctx->stream;
   // consumer-side wait limit (a short one is how tests make the kernel give up)
   const int wl = ctx->cfg.wait_limit_log2;
   t->prm.wait = t->tprm.wait = (wl > 0) ? (1LL << std::min(wl, 62)) : attn::tc::kWaitCycles;
   // the kind buffers are indexed by pair kind k (0,1,2); kinds with no products pass null
-  prep_x_kernel<<<tile_grid(m), dim3(kTile, 8), 0, st>>>(x, m[0], m[1], m[2], t->R[0] ? t->x[0].as<__nv_bfloat16>() : nullptr,
-                                          t->R[1] ? t->x[1].as<__nv_bfloat16>() : nullptr,
-                                          (t->R[2] || t->nt) ? t->x[2].as<__nv_bfloat16>() : nullptr);
+  void* xk[3];
+  for (int k = 0; k < 3; ++k) xk[k] = (t->R[k] || (k == 2 && t->nt)) ? t->x[k].p : nullptr;
+  if (tf)
+    prep_x_kernel<float><<<tile_grid(m), dim3(kTile, 8), 0, st>>>(x, m[0], m[1], m[2], static_cast<float*>(xk[0]),
+                                                                   static_cast<float*>(xk[1]), static_cast<float*>(xk[2]));
+  else
+    prep_x_kernel<__nv_bfloat16><<<tile_grid(m), dim3(kTile, 8), 0, st>>>(
+        x, m[0], m[1], m[2], static_cast<__nv_bfloat16*>(xk[0]), static_cast<__nv_bfloat16*>(xk[1]),
+        static_cast<__nv_bfloat16*>(xk[2]));
   ctx->launches++;
   auto zero_split_outputs = [&]() {
     for (int k = 0; k < 3; ++k)
       if (t->R[k]) ATTN_CHECK_CUDA(cudaMemsetAsync(t->y[k].p, 0, sizeof(float) * (size_t)V, st));
   };
-  const std::array<int, 6> key = {m[0], m[1], m[2], t->R[0], t->R[1], t->R[2]};
+  const std::array<int, 7> key = {m[0], m[1], m[2], t->R[0], t->R[1], t->R[2], tf ? 1 : 0};
   if (t->grid > 0 && !t->tuned) {
     auto hit = ctx->tc_split_cache.find(key);
     double fl_all = 0.0;
@@ -665,7 +741,8 @@ void attn_heff::apply_bf16(const double* x, double* y) {
   }
   if (t->grid > 0 && !t->tuned) {
     // Autotuner: time the candidate product splits on this H_eff's real input and
-    // keep the fastest (one-off per shape and product counts, at the first BF16 application).
+    // keep the fastest (one-off per shape, product counts and operand type, at the
+    // first tensor-core application).
     cudaEvent_t e0, e1;
     ATTN_CHECK_CUDA(cudaEventCreate(&e0));
     ATTN_CHECK_CUDA(cudaEventCreate(&e1));
@@ -678,7 +755,7 @@ void attn_heff::apply_bf16(const double* x, double* y) {
       for (int rep = 0; rep < 3; ++rep) {
         if (t->split_any()) zero_split_outputs();
         ATTN_CHECK_CUDA(cudaEventRecord(e0, st));
-        sandwich_tc_kernel<false><<<t->grid, kThreads, t->smem, st>>>(t->maps, t->prm);
+        launch_sandwich(false, t, t->grid, t->maps, t->prm, st);
         ATTN_CHECK_CUDA(cudaEventRecord(e1, st));
         ATTN_CHECK_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -705,7 +782,7 @@ void attn_heff::apply_bf16(const double* x, double* y) {
       if (has_hint[s]) fl += 2.0 * m[s] * V;
     if (t->split_any()) zero_split_outputs();
     ctx->prof_begin(0);
-    sandwich_tc_kernel<false><<<t->grid, kThreads, t->smem, st>>>(t->maps, t->prm);
+    launch_sandwich(false, t, t->grid, t->maps, t->prm, st);
     ctx->prof_end(0, fl);
     ctx->launches++;
   }
@@ -713,18 +790,19 @@ void attn_heff::apply_bf16(const double* x, double* y) {
     // three-link products, one chunk of products at a time: W = x x_2 C_r on the
     // TN GEMM, then Y01[c] += A_r W_r[c] B_r^T on the per-product kernel
     const int P = m[0], Q = m[1], S = m[2];
+    const size_t es = t->es();
     if (!t->R[0]) ATTN_CHECK_CUDA(cudaMemsetAsync(t->y[0].p, 0, sizeof(float) * (size_t)V, st));
     for (int r0 = 0; r0 < t->nt; r0 += t->tchunk) {
       const int Rc = std::min(t->tchunk, t->nt - r0);
       TnOperand A;  // x as [a b][c]: rows P Q, K = S
-      A.p = t->x[2].as<__nv_bfloat16>(); A.K = S; A.rows = P * Q; A.batches = 1; A.ld = S; A.bstride = 0;
+      A.p = t->x[2].p; A.tf = tf; A.K = S; A.rows = P * Q; A.batches = 1; A.ld = S; A.bstride = 0;
       TnOperand B;  // C_r as [r][c][c']
-      B.p = t->t2.as<__nv_bfloat16>() + (long)r0 * S * S; B.K = S; B.rows = S; B.batches = Rc; B.ld = S;
-      B.bstride = (long)S * S;
+      B.p = t->t2.as<uint8_t>() + es * (size_t)r0 * S * S; B.tf = tf; B.K = S; B.rows = S; B.batches = Rc;
+      B.ld = S; B.bstride = (long)S * S;
       TnParams g;
       g.M = P * Q; g.N = S; g.K = S; g.Bhi = Rc; g.Blo = 1; g.a_bhi = 0; g.b_bhi = 1;
-      g.C = t->w.p; g.c_type = 1; g.c_rs = 1; g.c_cs = (long)P * Q; g.c_bhi = V;
-      tn_gemm_bf16(ctx, A, B, g, t->err);
+      g.C = t->w.p; g.c_type = tf ? 3 : 1; g.c_rs = 1; g.c_cs = (long)P * Q; g.c_bhi = V;
+      tn_gemm(ctx, A, B, g, t->err);
       KindParams& kp = t->tprm.kind[0];
       kp.R = Rc;
       const int pairs = (S + 1) / 2;
@@ -732,10 +810,10 @@ void attn_heff::apply_bf16(const double* x, double* y) {
       kp.rsplit = f;
       const int grid = pairs * f;
       TcMaps mp = t->tmaps;
-      encode_map(&mp.a[0], t->t0.as<__nv_bfloat16>() + (long)r0 * P * P, P, P, Rc, 128);
-      encode_map(&mp.b[0], t->t1.as<__nv_bfloat16>() + (long)r0 * Q * Q, Q, Q, Rc, 128);
+      encode_map(&mp.a[0], t->t0.as<uint8_t>() + es * (size_t)r0 * P * P, P, P, Rc, 128, tf);
+      encode_map(&mp.b[0], t->t1.as<uint8_t>() + es * (size_t)r0 * Q * Q, Q, Q, Rc, 128, tf);
       ctx->prof_begin(0);
-      sandwich_tc_kernel<true><<<grid, kThreads, t->smem, st>>>(mp, t->tprm);
+      launch_sandwich(true, t, grid, mp, t->tprm, st);
       ctx->prof_end(0, (double)Rc * 2.0 * (P + Q) * V);
       ctx->launches++;
     }
@@ -747,3 +825,6 @@ void attn_heff::apply_bf16(const double* x, double* y) {
   ctx->launches++;
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
+
+void attn_heff::apply_bf16(const double* x, double* y) { apply_tc(x, y, false); }
+void attn_heff::apply_tf32(const double* x, double* y) { apply_tc(x, y, true); }

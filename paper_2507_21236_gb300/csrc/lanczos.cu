@@ -9,6 +9,11 @@
 // Gaussian elimination with partial pivoting) for the eigenvector. Stops when
 // the Ritz residual beta_k |y_k| < tol |theta|, on breakdown, or at `depth`.
 //
+// The Krylov basis is stored block-interleaved: for every chunk of 256 elements the
+// chunks of all basis vectors lie next to each other, so each Gram-Schmidt pass over
+// the basis reads one contiguous stream (vectors 16.8 MB apart at m = 128 made one
+// stream per vector); a contiguous copy of the newest vector feeds the matvec.
+//
 // The whole recurrence is device-resident: beta_k, the Ritz solve and the
 // stop decision are taken by a one-thread kernel after every step and kept in
 // device memory; kernels after the stop see the flag and return, and the
@@ -32,20 +37,26 @@ constexpr int LB = 512;  // blocks for the vector reductions
 constexpr int S_ALPHA = 0, S_BETA = 64, S_TMP = 128, S_DONE = 129, S_NK = 130, S_THETA = 131, S_RESID = 132,
               S_Y = 192, S_H = 320, S_H2 = 400, S_SIZE = 512;
 
+// Element e of basis vector i: block-interleaved with capacity D (chunks of LT = 256
+// elements, chunk c of vector i at (c D + i) LT), or contiguous (D = 0: vector i at i V).
+__device__ __forceinline__ long bidx(int i, long e, long V, int D) {
+  return D ? (((e >> 8) * D + i) << 8) + (e & 255) : (long)i * V + e;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
 // part[b][i] = partial of <basis_i, w> over block b's grid-stride elements.
-__global__ void multi_dot_partial(const double* basis, int nvec, long V, const double* w, double* part,
+__global__ void multi_dot_partial(const double* basis, int nvec, long V, int D, const double* w, double* part,
                                   const double* done) {
   if (done && *done != 0.0) return;
   __shared__ double sh[LT / 32];
   for (int i = 0; i < nvec; ++i) {
-    const double* v = basis + (long)i * V;
     double s = 0.0;
-    for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) s = fma(v[e], w[e], s);
+    for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT)
+      s = fma(basis[bidx(i, e, V, D)], w[e], s);
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -77,12 +88,12 @@ __global__ void multi_dot_reduce(const double* part, int nb, int nvec, double* o
 }
 
 // w -= sum_i coef[i] * basis_i
-__global__ void multi_axpy(double* w, const double* basis, const double* coef, int nvec, long V, double sign,
+__global__ void multi_axpy(double* w, const double* basis, const double* coef, int nvec, long V, int D, double sign,
                            const double* done) {
   if (done && *done != 0.0) return;
   for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) {
     double v = w[e];
-    for (int i = 0; i < nvec; ++i) v = fma(-sign * coef[i], basis[(long)i * V + e], v);
+    for (int i = 0; i < nvec; ++i) v = fma(-sign * coef[i], basis[bidx(i, e, V, D)], v);
     w[e] = v;
   }
 }
@@ -120,7 +131,7 @@ __device__ __forceinline__ void block_sum_store(double (&acc)[NV], int n, double
 
 // (A) part[b][i] = block b's share of <basis_i, w>
 template <int NV, int U>
-__global__ void __launch_bounds__(LT) cgs_dot(const double* __restrict__ basis, int n, long V,
+__global__ void __launch_bounds__(LT) cgs_dot(const double* __restrict__ basis, int n, long V, int D,
                                               const double* __restrict__ w, double* part, const double* done) {
   if (done && *done != 0.0) return;
   double acc[NV];
@@ -136,7 +147,7 @@ __global__ void __launch_bounds__(LT) cgs_dot(const double* __restrict__ basis, 
       if (i < n) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (e0 + u * stride < V) acc[i] = fma(basis[(long)i * V + e0 + u * stride], we[u], acc[i]);
+          if (e0 + u * stride < V) acc[i] = fma(basis[bidx(i, e0 + u * stride, V, D)], we[u], acc[i]);
       }
   }
   block_sum_store<NV>(acc, n, part + (long)blockIdx.x * n);
@@ -145,7 +156,8 @@ __global__ void __launch_bounds__(LT) cgs_dot(const double* __restrict__ basis, 
 // (B) w -= sum_i h_i basis_i, then part[b][i] = block share of <basis_i, w_new>
 template <int NV, int U>
 __global__ void __launch_bounds__(LT) cgs_axpy_dot(double* __restrict__ w, const double* __restrict__ basis,
-                                                   const double* h, int n, long V, double* part, const double* done) {
+                                                   const double* h, int n, long V, int D, double* part,
+                                                   const double* done) {
   if (done && *done != 0.0) return;
   __shared__ double c[NV];
   if (threadIdx.x < NV) c[threadIdx.x] = threadIdx.x < n ? h[threadIdx.x] : 0.0;
@@ -161,7 +173,7 @@ __global__ void __launch_bounds__(LT) cgs_axpy_dot(double* __restrict__ w, const
       const long e = e0 + u * stride;
       v[u] = e < V ? w[e] : 0.0;
 #pragma unroll
-      for (int i = 0; i < NV; ++i) b[u][i] = (i < n && e < V) ? basis[(long)i * V + e] : 0.0;
+      for (int i = 0; i < NV; ++i) b[u][i] = (i < n && e < V) ? basis[bidx(i, e, V, D)] : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -181,7 +193,8 @@ __global__ void __launch_bounds__(LT) cgs_axpy_dot(double* __restrict__ w, const
 // (C) w -= sum_i h_i basis_i, then part[b] = block share of ||w_new||^2
 template <int NV, int U>
 __global__ void __launch_bounds__(LT) cgs_axpy_norm(double* __restrict__ w, const double* __restrict__ basis,
-                                                    const double* h, int n, long V, double* part, const double* done) {
+                                                    const double* h, int n, long V, int D, double* part,
+                                                    const double* done) {
   if (done && *done != 0.0) return;
   __shared__ double c[NV];
   if (threadIdx.x < NV) c[threadIdx.x] = threadIdx.x < n ? h[threadIdx.x] : 0.0;
@@ -197,7 +210,7 @@ __global__ void __launch_bounds__(LT) cgs_axpy_norm(double* __restrict__ w, cons
       if (i < n) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (e0 + u * stride < V) v[u] = fma(-c[i], basis[(long)i * V + e0 + u * stride], v[u]);
+          if (e0 + u * stride < V) v[u] = fma(-c[i], basis[bidx(i, e0 + u * stride, V, D)], v[u]);
       }
 #pragma unroll
     for (int u = 0; u < U; ++u)
@@ -211,11 +224,11 @@ __global__ void __launch_bounds__(LT) cgs_axpy_norm(double* __restrict__ w, cons
 
 // out = sum_{i < n} coef[i] * basis_i with n = nvec, or (int)*nvec_dev if given
 __global__ void combine(double* out, const double* basis, const double* coef, int nvec, const double* nvec_dev,
-                        long V) {
+                        long V, int D) {
   const int n = nvec_dev ? (int)(*nvec_dev) : nvec;
   for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) {
     double v = 0.0;
-    for (int i = 0; i < n; ++i) v = fma(coef[i], basis[(long)i * V + e], v);
+    for (int i = 0; i < n; ++i) v = fma(coef[i], basis[bidx(i, e, V, D)], v);
     out[e] = v;
   }
 }
@@ -226,6 +239,19 @@ __global__ void scale_by_norm(double* dst, const double* src, const double* nrm_
   double n = sqrt(*nrm_sq);
   double inv = n > 0.0 ? 1.0 / n : 0.0;
   for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) dst[e] = src[e] * inv;
+}
+
+// The same into slot i of the interleaved basis (capacity D) and into the contiguous vk.
+__global__ void scale_into_basis(double* basis, int i, int D, double* vk, const double* src, const double* nrm_sq,
+                                 long V, const double* done) {
+  if (done && *done != 0.0) return;
+  double n = sqrt(*nrm_sq);
+  double inv = n > 0.0 ? 1.0 / n : 0.0;
+  for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) {
+    const double v = src[e] * inv;
+    basis[bidx(i, e, V, D)] = v;
+    vk[e] = v;
+  }
 }
 
 // Number of eigenvalues of the tridiagonal (a, b) smaller than x.
@@ -376,24 +402,24 @@ __global__ void lz_init(double* S) {
 inline int vgrid(long V) { return (int)std::max<long>(1, std::min<long>((V + LT - 1) / LT, LB)); }
 
 template <int NV, int U>
-void cgs2_launch(cudaStream_t s, const double* B, double* W, double* S, int n, long V, int nb, double* part,
+void cgs2_launch(cudaStream_t s, const double* B, int D, double* W, double* S, int n, long V, int nb, double* part,
                  const double* done) {
-  cgs_dot<NV, U><<<nb, LT, 0, s>>>(B, n, V, W, part, done);
+  cgs_dot<NV, U><<<nb, LT, 0, s>>>(B, n, V, D, W, part, done);
   multi_dot_reduce<<<n, LT, 0, s>>>(part, nb, n, S + S_H, nullptr, done);
-  cgs_axpy_dot<NV, U><<<nb, LT, 0, s>>>(W, B, S + S_H, n, V, part, done);
+  cgs_axpy_dot<NV, U><<<nb, LT, 0, s>>>(W, B, S + S_H, n, V, D, part, done);
   multi_dot_reduce<<<n, LT, 0, s>>>(part, nb, n, S + S_H2, nullptr, done);
-  cgs_axpy_norm<NV, U><<<nb, LT, 0, s>>>(W, B, S + S_H2, n, V, part, done);
+  cgs_axpy_norm<NV, U><<<nb, LT, 0, s>>>(W, B, S + S_H2, n, V, D, part, done);
   multi_dot_reduce<<<1, LT, 0, s>>>(part, nb, 1, S + S_TMP, nullptr, done);
 }
 
 // One CGS2 step against n <= kFusedMax basis vectors (six launches).
-void cgs2_fused(cudaStream_t s, const double* B, double* W, double* S, int n, long V, int nb, double* part,
+void cgs2_fused(cudaStream_t s, const double* B, int D, double* W, double* S, int n, long V, int nb, double* part,
                 const double* done) {
-  if (n <= 4) cgs2_launch<4, 4>(s, B, W, S, n, V, nb, part, done);
-  else if (n <= 8) cgs2_launch<8, 2>(s, B, W, S, n, V, nb, part, done);
-  else if (n <= 12) cgs2_launch<12, 2>(s, B, W, S, n, V, nb, part, done);
-  else if (n <= 16) cgs2_launch<16, 1>(s, B, W, S, n, V, nb, part, done);
-  else cgs2_launch<24, 1>(s, B, W, S, n, V, nb, part, done);
+  if (n <= 4) cgs2_launch<4, 4>(s, B, D, W, S, n, V, nb, part, done);
+  else if (n <= 8) cgs2_launch<8, 2>(s, B, D, W, S, n, V, nb, part, done);
+  else if (n <= 12) cgs2_launch<12, 2>(s, B, D, W, S, n, V, nb, part, done);
+  else if (n <= 16) cgs2_launch<16, 1>(s, B, D, W, S, n, V, nb, part, done);
+  else cgs2_launch<24, 1>(s, B, D, W, S, n, V, nb, part, done);
 }
 
 // Blocks for the fused streaming passes: enough resident warps on every SM to
@@ -408,11 +434,11 @@ int fused_grid(long V) {
   return (int)std::max<long>(1, std::min<long>((V + LT - 1) / LT, 4L * sms));
 }
 
-void multi_dot_g(attn_ctx* ctx, const double* basis, int nvec, long V, const double* w, double* out, double* accum,
-                 const double* done) {
+void multi_dot_g(attn_ctx* ctx, const double* basis, int nvec, long V, int D, const double* w, double* out,
+                 double* accum, const double* done) {
   const int nb = vgrid(V);
   ctx->partials.reserve(sizeof(double) * (size_t)nb * std::max(nvec, 1));
-  multi_dot_partial<<<nb, LT, 0, ctx->stream>>>(basis, nvec, V, w, ctx->partials.as<double>(), done);
+  multi_dot_partial<<<nb, LT, 0, ctx->stream>>>(basis, nvec, V, D, w, ctx->partials.as<double>(), done);
   multi_dot_reduce<<<nvec, LT, 0, ctx->stream>>>(ctx->partials.as<double>(), nb, nvec, out, accum, done);
   ctx->launches += 2;
   ATTN_CHECK_CUDA(cudaGetLastError());
@@ -421,18 +447,18 @@ void multi_dot_g(attn_ctx* ctx, const double* basis, int nvec, long V, const dou
 }  // namespace
 
 void multi_dot(attn_ctx* ctx, const double* basis, int nvec, long V, const double* w, double* out, double* accum) {
-  multi_dot_g(ctx, basis, nvec, V, w, out, accum, nullptr);
+  multi_dot_g(ctx, basis, nvec, V, 0, w, out, accum, nullptr);
 }
 
 void multi_axpy_dev(attn_ctx* ctx, double* w, const double* basis, const double* coef, int nvec, long V,
                     double sign) {
-  multi_axpy<<<vgrid(V), LT, 0, ctx->stream>>>(w, basis, coef, nvec, V, sign, nullptr);
+  multi_axpy<<<vgrid(V), LT, 0, ctx->stream>>>(w, basis, coef, nvec, V, 0, sign, nullptr);
   ctx->launches++;
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
 
 void combine_dev(attn_ctx* ctx, double* out, const double* basis, const double* coef, int nvec, long V) {
-  combine<<<vgrid(V), LT, 0, ctx->stream>>>(out, basis, coef, nvec, nullptr, V);
+  combine<<<vgrid(V), LT, 0, ctx->stream>>>(out, basis, coef, nvec, nullptr, V, 0);
   ctx->launches++;
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
@@ -447,19 +473,25 @@ void normalise_dev(attn_ctx* ctx, double* dst, const double* src, long V, double
 void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol, LanczosWork& w,
                      int host_check_every) {
   ATTN_REQUIRE(depth >= 1 && depth <= 60, ATTN_EINVAL, "Lanczos depth must be in 1..60");
-  w.basis.reserve(sizeof(double) * (size_t)(depth + 1) * V);
+  const int D = depth + 1;                 // basis capacity
+  const long chunks = (V + LT - 1) / LT;   // interleaving granule: LT elements
+  w.basis.reserve(sizeof(double) * (size_t)D * chunks * LT);
   w.wvec.reserve(sizeof(double) * (size_t)V);
+  w.vk.reserve(sizeof(double) * (size_t)V);
   w.scal.reserve(sizeof(double) * S_SIZE);
   double* B = w.basis.as<double>();
   double* W = w.wvec.as<double>();
+  double* vk = w.vk.as<double>();
   double* S = w.scal.as<double>();
   double* done = S + S_DONE;
   cudaStream_t s = ctx->stream;
   lz_init<<<1, 1, 0, s>>>(S);
   ctx->launches++;
-  normalise_dev(ctx, B, x, V, S + S_TMP);
+  // v_0 = x / |x| into basis slot 0 and the contiguous matvec input
+  multi_dot_g(ctx, x, 1, V, 0, x, S + S_TMP, nullptr, nullptr);
+  scale_into_basis<<<vgrid(V), LT, 0, s>>>(B, 0, D, vk, x, S + S_TMP, V, nullptr);
+  ctx->launches++;
   for (int k = 0; k < depth; ++k) {
-    double* vk = B + (long)k * V;
     apply(vk, W);
     // w -= sum_i <v_i, w> v_i over the whole basis, twice; the coefficient of
     // v_k is alpha_k and those of v_{k-1} and older vectors take the place of
@@ -468,20 +500,20 @@ void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int 
     if (n <= kFusedMax) {
       const int nb = fused_grid(V);
       ctx->partials.reserve(sizeof(double) * (size_t)nb * n);
-      cgs2_fused(s, B, W, S, n, V, nb, ctx->partials.as<double>(), done);
+      cgs2_fused(s, B, D, W, S, n, V, nb, ctx->partials.as<double>(), done);
       ctx->launches += 6;
     } else {
-      multi_dot_g(ctx, B, n, V, W, S + S_H, nullptr, done);
-      multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H, n, V, 1.0, done);
-      multi_dot_g(ctx, B, n, V, W, S + S_H2, nullptr, done);
-      multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H2, n, V, 1.0, done);
+      multi_dot_g(ctx, B, n, V, D, W, S + S_H, nullptr, done);
+      multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H, n, V, D, 1.0, done);
+      multi_dot_g(ctx, B, n, V, D, W, S + S_H2, nullptr, done);
+      multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H2, n, V, D, 1.0, done);
       ctx->launches += 2;
-      multi_dot_g(ctx, W, 1, V, W, S + S_TMP, nullptr, done);
+      multi_dot_g(ctx, W, 1, V, 0, W, S + S_TMP, nullptr, done);
     }
     lz_step<<<1, 32, 0, s>>>(S, k, depth, tol);
     ctx->launches++;
     if (k + 1 < depth) {
-      scale_by_norm<<<vgrid(V), LT, 0, s>>>(B + (long)(k + 1) * V, W, S + S_TMP, V, done);
+      scale_into_basis<<<vgrid(V), LT, 0, s>>>(B, k + 1, D, vk, W, S + S_TMP, V, done);
       ctx->launches++;
     }
     if (host_check_every > 0 && (k + 1) % host_check_every == 0 && k + 1 < depth) {
@@ -491,7 +523,7 @@ void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int 
       if (hd != 0.0) break;
     }
   }
-  combine<<<vgrid(V), LT, 0, s>>>(W, B, S + S_Y, 0, S + S_NK, V);
+  combine<<<vgrid(V), LT, 0, s>>>(W, B, S + S_Y, 0, S + S_NK, V, D);
   ctx->launches++;
   normalise_dev(ctx, x, W, V, S + S_TMP);
   ATTN_CHECK_CUDA(cudaGetLastError());

@@ -10,7 +10,8 @@ namespace attn {
 using MatVec = std::function<void(const double* x, double* y)>;
 
 struct LanczosWork {
-  DevBuf basis, wvec, scal;
+  DevBuf basis;  // block-interleaved Krylov basis (chunks of 256 elements, capacity depth + 1)
+  DevBuf wvec, vk, scal;  // residual vector, contiguous copy of the newest basis vector, scalars
 };
 
 struct LanczosResult {

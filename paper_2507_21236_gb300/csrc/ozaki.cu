@@ -70,6 +70,7 @@ constexpr uint32_t kIssuer0Diags = (1u << 0) | (1u << 3) | (1u << 5), kIssuer1Di
 
 struct OzParams {
   int M, N, nkb;           // rows of P, rows of Q, 64-wide K blocks
+  int nrtP, nrtQ;          // row tiles (of 128 and 64 rows) per operand batch entry
   int Bhi, Blo;            // batch entries b = bhi * Blo + blo
   int p_hi, p_lo, q_hi, q_lo;  // sliced-operand batch index = bhi * x_hi + blo * x_lo
   const int* EP;           // [batches of P][M] row exponents
@@ -81,8 +82,11 @@ struct OzParams {
   int* err;
 };
 
+// Slices are stored tiled: per operand batch entry, row tile, 64-wide K block and slice
+// one contiguous [tile rows][64] BF16 block, so that every TMA box is one contiguous
+// 16 KB (P) or 8 KB (Q) read rather than 128 or 64 strided 128-byte segments.
 struct OzMaps {
-  CUtensorMap p, q;  // [batches * 6][rows][Kpad] BF16, boxes {64, 128, 1} and {64, 64, 1}
+  CUtensorMap p, q;  // [((batch * nrt + tile) * nkb + kb) * 6 + s][tile rows][64], boxes {64, 128 / 64, 1}
 };
 
 __device__ __forceinline__ bool window_end(int d, int kb, int nkb) {
@@ -148,6 +152,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
 
   if (warp == 0 && lane == 0) {
     // ---- producer: per K block the six Q slices, then the six P slices
+    const int zP = (bp * p.nrtP + (int)blockIdx.y) * nkb * kSlices;
+    const int zQ = (bq * p.nrtQ + (int)blockIdx.x) * nkb * kSlices;
     int pst = 0, pissued = 0;
     uint32_t pph = 0;
     int qissued = 0;
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
       if (kb >= 2 && !mbar_wait(bar(QEMPTY + qb), ((kb >> 1) - 1) & 1, p.err, 61, abort_flag)) break;
       mbar_expect_tx(bar(QFULL + qb), (uint32_t)kQBufBytes);
       for (int s = 0; s < kSlices; ++s)
-        tma_load_3d(sQ + qb * kQBufBytes + s * kQBytes, &maps.q, 64 * kb, n0, bq * kSlices + s, bar(QFULL + qb));
+        tma_load_3d(sQ + qb * kQBufBytes + s * kQBytes, &maps.q, 0, 0, zQ + kb * kSlices + s, bar(QFULL + qb));
       qissued = kb + 1;
       for (int s = 0; s < kSlices; ++s) {
         if (pissued >= kPStages && !mbar_wait(bar(PEMPTY + pst), pph ^ 1u, p.err, 62, abort_flag)) {
@@ -165,7 +171,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
           break;
         }
         mbar_expect_tx(bar(PFULL + pst), (uint32_t)kPBytes);
-        tma_load_3d(sP + pst * kPBytes, &maps.p, 64 * kb, m0, bp * kSlices + s, bar(PFULL + pst));
+        tma_load_3d(sP + pst * kPBytes, &maps.p, 0, 0, zP + kb * kSlices + s, bar(PFULL + pst));
         ++pissued;
         if (++pst == kPStages) { pst = 0; pph ^= 1u; }
       }
@@ -348,16 +354,19 @@ __global__ void oz_exponent_kernel(OzView v, int* E) {
   }
 }
 
-// S[batch][s][row][Kpad] = slice s of 2^-E[row] entry, zero for k' >= K G. The
-// entry becomes the integer F = round(|x| 2^(47-E)) (|F| < 2^47, from the bits of
-// x, rounding half up), signed, then balanced base-256 digits from the bottom:
-// n_6 .. n_2 in [-128, 127], n_1 = the rest (|n_1| <= 128), F = sum_s n_s 2^(8(6-s)).
-__global__ void oz_slice_kernel(OzView v, const int* E, __nv_bfloat16* S, long Kpad) {
+// Slice s of 2^-E[row] entry, written tiled: element (batch, row, k) of slice s at
+// ((((batch nrt + row / TR) nkb + k / 64) 6 + s) TR + row % TR) 64 + k % 64, zero for
+// k >= K G and for the padding rows of the last tile. The entry becomes the integer
+// F = round(|x| 2^(47-E)) (|F| < 2^47, from the bits of x, rounding half up), signed,
+// then balanced base-256 digits from the bottom: n_6 .. n_2 in [-128, 127], n_1 = the
+// rest (|n_1| <= 128), F = sum_s n_s 2^(8(6-s)).
+__global__ void oz_slice_kernel(OzView v, const int* E, __nv_bfloat16* S, long Kpad, int TR, int nrt) {
   __shared__ long long t[kT][kT + 1];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const long r0 = (long)blockIdx.y * kT, k0 = (long)blockIdx.x * kT;
   const int batch = blockIdx.z, bh = batch / v.nblo, bl = batch % v.nblo;
   const long Kt = (long)v.K * v.G;
+  const long nkb = Kpad / 64;
   const bool kfast = (v.sK == 1 && v.sR != 1);
   for (int i = ty; i < kT; i += 8) {
     const long r = kfast ? r0 + i : r0 + tx, k = kfast ? k0 + tx : k0 + i;
@@ -369,9 +378,9 @@ __global__ void oz_slice_kernel(OzView v, const int* E, __nv_bfloat16* S, long K
   __syncthreads();
   for (int i = ty; i < kT; i += 8) {
     const long r = r0 + i, k = k0 + tx;
-    if (r >= v.rows || k >= Kpad) continue;
+    if (r >= (long)nrt * TR || k >= Kpad) continue;
     const long long b = t[i][tx];
-    const int e = E[(long)batch * v.rows + r];
+    const int e = r < v.rows ? E[(long)batch * v.rows + r] : kEmptyRow;
     long long F = 0;
     if ((b & 0x7FFFFFFFFFFFFFFFll) && e != kEmptyRow) {
       const int ef = (int)((b >> 52) & 0x7FF);
@@ -381,21 +390,23 @@ __global__ void oz_slice_kernel(OzView v, const int* E, __nv_bfloat16* S, long K
       else if (sh > -64) F = (sh == -63 ? 0ll : (mant + (1ll << (-sh - 1))) >> (-sh));
       if (b < 0) F = -F;
     }
-    __nv_bfloat16* out = S + ((long)batch * kSlices * v.rows + r) * Kpad + k;
+    __nv_bfloat16* out = S + ((((long)batch * nrt + r / TR) * nkb + (k >> 6)) * kSlices * TR + r % TR) * 64 + (k & 63);
+    const long sstride = (long)TR * 64;
 #pragma unroll
-    for (int s = kSlices - 1; s >= 1; --s) {
+    for (int sl = kSlices - 1; sl >= 1; --sl) {
       const int d = (int)(((F & 255) ^ 128) - 128);  // balanced digit in [-128, 127]
-      out[(long)s * v.rows * Kpad] = __int2bfloat16_rn(d);  // exact: |d| <= 128
+      out[(long)sl * sstride] = __int2bfloat16_rn(d);  // exact: |d| <= 128
       F = (F - d) >> 8;
     }
     out[0] = __int2bfloat16_rn((int)F);
   }
 }
 
-void encode_slices(CUtensorMap* map, const __nv_bfloat16* p, long Kpad, int rows, long nslices, int box_rows) {
-  cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows, (cuuint64_t)nslices};
-  cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)Kpad * rows * 2};
-  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+// Map over tiled slices: [nz][tile rows][64] BF16 with a {64, tile rows, 1} box.
+void encode_slices(CUtensorMap* map, const __nv_bfloat16* p, int tile_rows, long nz) {
+  cuuint64_t dims[3] = {64, (cuuint64_t)tile_rows, (cuuint64_t)nz};
+  cuuint64_t strides[2] = {128, (cuuint64_t)tile_rows * 128};
+  cuuint32_t box[3] = {64, (cuuint32_t)tile_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = tensor_map_encoder()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(p), dims,
                                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -407,10 +418,13 @@ int grid_cap(long n) { return (int)std::max<long>(1, std::min<long>(n, 65535)); 
 
 }  // namespace
 
-void ozaki_slice(attn_ctx* ctx, const OzView& v, long Kpad, DevBuf& slices, DevBuf& exps) {
+void ozaki_slice(attn_ctx* ctx, const OzView& v, long Kpad, int tile_rows, DevBuf& slices, DevBuf& exps) {
   const long nb = (long)v.nbhi * v.nblo;
   ATTN_REQUIRE(nb <= 65535, ATTN_EUNSUPPORTED, "too many operand batches for the split GEMM");
-  slices.reserve(sizeof(__nv_bfloat16) * (size_t)(nb * kSlices * v.rows * Kpad));
+  const int nrt = (v.rows + tile_rows - 1) / tile_rows;
+  const long padded = (long)nrt * tile_rows;
+  ATTN_REQUIRE(nb * nrt * (Kpad / 64) * kSlices < (1L << 31), ATTN_EUNSUPPORTED, "operand too large for the split GEMM");
+  slices.reserve(sizeof(__nv_bfloat16) * (size_t)(nb * kSlices * padded * Kpad));
   exps.reserve(sizeof(int) * (size_t)(nb * v.rows));
   cudaStream_t st = ctx->stream;
   const long ne = nb * v.rows;
@@ -424,9 +438,9 @@ void ozaki_slice(attn_ctx* ctx, const OzView& v, long Kpad, DevBuf& slices, DevB
   dim3 ge((unsigned)std::min<long>(kt, std::max<long>(1, 8192 / std::max<long>(rt * nb, 1))), (unsigned)rt,
           (unsigned)nb);
   oz_exponent_kernel<<<ge, blk, 0, st>>>(v, exps.as<int>());
-  dim3 gs((unsigned)((Kpad + kT - 1) / kT), (unsigned)rt, (unsigned)nb);
+  dim3 gs((unsigned)((Kpad + kT - 1) / kT), (unsigned)((padded + kT - 1) / kT), (unsigned)nb);
   ATTN_REQUIRE(gs.x <= 2147483647u, ATTN_EUNSUPPORTED, "K too large for the split GEMM");
-  oz_slice_kernel<<<gs, blk, 0, st>>>(v, exps.as<int>(), slices.as<__nv_bfloat16>(), Kpad);
+  oz_slice_kernel<<<gs, blk, 0, st>>>(v, exps.as<int>(), slices.as<__nv_bfloat16>(), Kpad, tile_rows, nrt);
   ctx->launches += 3;
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
@@ -483,13 +497,16 @@ void gemm_f64_ozaki(attn_ctx* ctx, const GemmF64& g0) {
     p.G = q.G = gn;
     const long Kt = (long)g0.K * gn;
     const long Kpad = (Kt + 63) / 64 * 64;
-    ozaki_slice(ctx, p, Kpad, ctx->oz_ws[0], ctx->oz_ws[1]);
-    ozaki_slice(ctx, q, Kpad, ctx->oz_ws[2], ctx->oz_ws[3]);
+    ozaki_slice(ctx, p, Kpad, 128, ctx->oz_ws[0], ctx->oz_ws[1]);
+    ozaki_slice(ctx, q, Kpad, kQRows, ctx->oz_ws[2], ctx->oz_ws[3]);
+    const int nrtP = (M + 127) / 128, nrtQ = (N + kQRows - 1) / kQRows;
+    const long nkb = Kpad / 64;
     OzMaps maps;
-    encode_slices(&maps.p, ctx->oz_ws[0].as<__nv_bfloat16>(), Kpad, M, (long)p.nbhi * p.nblo * kSlices, 128);
-    encode_slices(&maps.q, ctx->oz_ws[2].as<__nv_bfloat16>(), Kpad, N, (long)q.nbhi * q.nblo * kSlices, kQRows);
+    encode_slices(&maps.p, ctx->oz_ws[0].as<__nv_bfloat16>(), 128, (long)p.nbhi * p.nblo * nrtP * nkb * kSlices);
+    encode_slices(&maps.q, ctx->oz_ws[2].as<__nv_bfloat16>(), kQRows, (long)q.nbhi * q.nblo * nrtQ * nkb * kSlices);
     OzParams prm;
-    prm.M = M; prm.N = N; prm.nkb = (int)(Kpad / 64);
+    prm.M = M; prm.N = N; prm.nkb = (int)nkb;
+    prm.nrtP = nrtP; prm.nrtQ = nrtQ;
     prm.Bhi = g0.Bhi; prm.Blo = g0.Blo;
     prm.p_hi = P.sBhi ? p.nblo : 0; prm.p_lo = P.sBlo ? 1 : 0;
     prm.q_hi = Q.sBhi ? q.nblo : 0; prm.q_lo = Q.sBlo ? 1 : 0;

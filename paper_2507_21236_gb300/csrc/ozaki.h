@@ -16,9 +16,10 @@ struct OzView {
   int nbhi = 1, nblo = 1;  // distinct batch entries of this operand
 };
 
-// Row exponents E (|entry| < 2^E per row; -2000 for a zero row) and six BF16
-// slices [batch][6][rows][Kpad] of 2^-E times each row (Kpad >= K G, a multiple of 64).
-void ozaki_slice(attn_ctx* ctx, const OzView& v, long Kpad, DevBuf& slices, DevBuf& exps);
+// Row exponents E (|entry| < 2^E per row; -2000 for a zero row) and six BF16 slices
+// of 2^-E times each row (Kpad >= K G, a multiple of 64), stored tiled: per batch entry,
+// tile of tile_rows rows and 64-wide K block, the six [tile_rows][64] slice blocks.
+void ozaki_slice(attn_ctx* ctx, const OzView& v, long Kpad, int tile_rows, DevBuf& slices, DevBuf& exps);
 
 // The GemmF64 contraction C = alpha sum_g A_g B_g + beta C, computed from the
 // slices' exact BF16 products (normwise error about (K + 2) 2^-46 of the row scales).

@@ -453,10 +453,8 @@ double attn_state::local_step(int n) {
     double* v = tmpT.as<double>();
     copy_f64(ctx, v, tensor(n), V);
     // nodes whose links are too small for the tensor-core tiles use FP64 matvecs
-    const attn_dtype dt = (cfg.matvec_dtype == ATTN_BF16 && tc_supported(h)) ? ATTN_BF16 : ATTN_F64;
-    MatVec mv_lo = [&](const double* a, double* b) {
-      if (dt == ATTN_BF16) h->apply_bf16(a, b); else h->apply_f64(a, b);
-    };
+    const attn_dtype dt = (cfg.matvec_dtype != ATTN_F64 && tc_supported(h)) ? cfg.matvec_dtype : ATTN_F64;
+    MatVec mv_lo = [&](const double* a, double* b) { h->apply(a, b, dt); };
     MatVec mv64 = [&](const double* a, double* b) { h->apply_f64(a, b); };
     // current energy (FP64): known from the last local step unless H' or a tensor changed since
     double e_cur = energy_known;

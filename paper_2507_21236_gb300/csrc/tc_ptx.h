@@ -74,6 +74,33 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// kind::tf32 instruction descriptor: D = F32, A = B = TF32 (format code 2), both K-major.
+__device__ __forceinline__ uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// One K step of 8 TF32 elements (32 bytes, like 16 BF16 ones): A and B in shared memory.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// The same with A (M x 8 FP32 values, one row per lane) read from tensor memory.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// Round an FP32 value to TF32 (nearest, ties away from zero): the low 13 mantissa bits become zero.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -160,6 +187,40 @@ __device__ __forceinline__ void mma4_ts(uint32_t d, uint32_t a_tmem, uint64_t db
   mma_bf16_ts(d, a_tmem + 8, db + 2, idesc, 1u);
   mma_bf16_ts(d, a_tmem + 16, db + 4, idesc, 1u);
   mma_bf16_ts(d, a_tmem + 24, db + 6, idesc, 1u);
+}
+
+// Operand-type dispatch of the tcgen05 kernels: kTF = false -> BF16 (kind::f16, 16
+// elements per K step), true -> TF32 (kind::tf32, 8 elements per K step). Either way
+// a K step is 32 bytes and a 128-byte swizzled K block holds four of them.
+template <bool kTF>
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (kTF) mma_tf32(d, a, b, idesc, acc);
+  else mma_bf16(d, a, b, idesc, acc);
+}
+template <bool kTF>
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (kTF) mma_tf32_ts(d, a_tmem, b, idesc, acc);
+  else mma_bf16_ts(d, a_tmem, b, idesc, acc);
+}
+template <bool kTF>
+__device__ __forceinline__ void mma4_ss_t(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc_first) {
+  mma_ss<kTF>(d, da, db, idesc, acc_first);
+  mma_ss<kTF>(d, da + 2, db + 2, idesc, 1u);
+  mma_ss<kTF>(d, da + 4, db + 4, idesc, 1u);
+  mma_ss<kTF>(d, da + 6, db + 6, idesc, 1u);
+}
+// TS form: A advances 8 TMEM columns per K step (16 packed BF16, or 8 FP32 values).
+template <bool kTF>
+__device__ __forceinline__ void mma4_ts_t(uint32_t d, uint32_t a_tmem, uint64_t db, uint32_t idesc,
+                                          uint32_t acc_first) {
+  mma_ts<kTF>(d, a_tmem, db, idesc, acc_first);
+  mma_ts<kTF>(d, a_tmem + 8, db + 2, idesc, 1u);
+  mma_ts<kTF>(d, a_tmem + 16, db + 4, idesc, 1u);
+  mma_ts<kTF>(d, a_tmem + 24, db + 6, idesc, 1u);
+}
+template <bool kTF>
+__device__ __forceinline__ uint32_t idesc_of(int M, int N) {
+  return kTF ? idesc_tf32(M, N) : idesc_bf16(M, N);
 }
 // Barrier over a subset of the block's warps (id 1..15; id 0 is __syncthreads).
 __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {

@@ -156,21 +156,23 @@ def test_attn_below_ttn_at_equal_bond_dimension():
         attn.attn_state_destroy(st)
         attn.attn_model_destroy(mod)
         attn.attn_destroy(ctx)
-    # the first sweep is TTN-only in both runs (S_TTN = 1): identical arithmetic
-    assert out[0][0] == out[16][0]
+    # the first sweep is TTN-only in both runs (S_TTN = 1); with identity disentanglers
+    # mapped in, H' equals H but is split into other (equivalent) products
+    assert abs(out[0][0] - out[16][0]) <= 1e-12 * abs(out[0][0])
     print(f"E/site after {sweeps} sweeps: TTN {out[0][-1] / 64:.10f}, aTTN {out[16][-1] / 64:.10f}")
     assert out[16][-1] <= out[0][-1]
 
 
 def test_riemannian_de_update_matches_oracle():
     """de_method 1 (Sec. 4.1.2): Riemannian conjugate gradients on the GPU follow the
-    oracle's iteration from the identity to the same E_k (1e-10) and u (1e-6), and
+    oracle's iteration from the identity to the same E_k (1e-10) and u (1e-5), and
     stop at the MERA-like update's energy within 1e-8."""
     from oracle.de_update import optimise_de_riemannian
 
     attn, ctx, mod, st, ost, terms, tree, des = _pair(4, 8, 4)
     cfg = attn.attn_get_config(ctx)
     cfg.de_method = 1
+    cfg.de_max_iter = 60  # enough for the conjugate gradients to meet the relative-change stop
     attn.attn_set_config(ctx, cfg)
     attn.attn_map_hamiltonian(st)
     attn.attn_ttn_sweep(st)
@@ -179,12 +181,14 @@ def test_riemannian_de_update_matches_oracle():
     attn.attn_de_update(st)
     en = attn.attn_de_energies(st, len(des))
     for k, p in enumerate(build_problems(ost, terms, des)):
-        u_ref, hist = optimise_de_riemannian(p, np.eye(4))
+        u_ref, hist = optimise_de_riemannian(p, np.eye(4), max_iter=60)
         assert abs(en[k, 0] - hist[0]) <= 1e-12 * abs(hist[0])
         assert abs(en[k, 1] - hist[-1]) <= 1e-10 * abs(hist[-1]), k
         u = attn.attn_de_get(st, k)
         assert np.abs(u.T @ u - np.eye(4)).max() < 1e-12
-        assert np.abs(u - u_ref).max() < 1e-6, k
+        # E_k is flat at its minimum: the disentanglers agree as the square root of the
+        # energy difference
+        assert np.abs(u - u_ref).max() < 1e-5, k
         assert abs(hist[-1] - optimise_de(p, np.eye(4))[1][-1]) <= 1e-8 * abs(hist[-1])
     attn.attn_state_destroy(st)
     attn.attn_model_destroy(mod)

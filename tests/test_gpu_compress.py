@@ -30,9 +30,10 @@ def test_compressed_heisenberg_heff_matches_oracle(L, m, n_de):
     rng = np.random.default_rng(4)
     us = [_orth(rng) for _ in des]
     raw = raw_tree_tensors(tree.shape, 1)
-    ost = TTNState.from_raw(tree, raw, products_of(map_terms(terms, des, us)))
     counts, energies = {}, {}
     for comp in (0, 1):
+        # a fresh oracle state per arm: centre moves change the gauge of the tensors
+        ost = TTNState.from_raw(tree, raw, products_of(map_terms(terms, des, us)))
         attn, ctx = lib_and_ctx({"compress_terms": comp})
         mod = attn.attn_model_tri_heisenberg(ctx, L, 1.0)
         st = attn.attn_state_create(ctx, mod, m, raw)
