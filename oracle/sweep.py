@@ -23,13 +23,23 @@ from .de_update import build_problems, optimise_de
 from .lanczos import lanczos_lowest
 
 
-def local_step(state, n, depth=20, tol=1e-13):
+def local_step(state, n, depth=20, tol=1e-13, term_by_term=False):
+    """``term_by_term`` applies H_eff one rank-1 product at a time (the definition of
+    Sec. 3.3.2) instead of one einsum per slot pattern: the same sum, and the only form
+    that stays affordable at m >= 32 (numpy evaluates the stacked einsum without
+    intermediates, at O(r m^6))."""
     state.move_centre(n)
-    stacked = state.heff_stacked(n)
     t = state.T[n]
+    if term_by_term:
+        terms = state.heff_terms(n)
 
-    def apply(x):
-        return state.heff_apply_stacked(x, stacked)
+        def apply(x):
+            return state.heff_apply(n, x, terms)
+    else:
+        stacked = state.heff_stacked(n)
+
+        def apply(x):
+            return state.heff_apply_stacked(x, stacked)
 
     e_cur = float(np.vdot(t, apply(t)) / np.vdot(t, t))
     theta, v, info = lanczos_lowest(apply, t, depth=depth, tol=tol)
@@ -39,18 +49,18 @@ def local_step(state, n, depth=20, tol=1e-13):
     return e_cur
 
 
-def ttn_sweep(state, depth=20, tol=1e-13, order=None):
+def ttn_sweep(state, depth=20, tol=1e-13, order=None, term_by_term=False):
     order = order or state.tree.post_order()
     e = None
     energies = []
     for n in order:
-        e = local_step(state, n, depth, tol)
+        e = local_step(state, n, depth, tol, term_by_term)
         energies.append(e)
     return e, energies
 
 
 def attn_ground_state(state, terms, des, n_sweeps, s_ttn=1, us=None, depth=20, tol=1e-13,
-                      de_max_iter=20, de_rel_dev=1e-12, log=None):
+                      de_max_iter=20, de_rel_dev=1e-12, log=None, term_by_term=False):
     """Run the schedule; returns (energies per sweep, disentanglers, local energies)."""
     us = [np.eye(4) for _ in des] if us is None else [u.copy() for u in us]
     out = []
@@ -62,7 +72,7 @@ def attn_ground_state(state, terms, des, n_sweeps, s_ttn=1, us=None, depth=20, t
             us = [optimise_de(p, u, de_max_iter, de_rel_dev)[0] for p, u in zip(probs, us)]
         mapped = map_terms(terms, des, us)
         state.set_products(products_of(mapped))
-        e, _ = ttn_sweep(state, depth, tol)
+        e, _ = ttn_sweep(state, depth, tol, term_by_term=term_by_term)
         out.append(e)
         if log:
             log(s, e)

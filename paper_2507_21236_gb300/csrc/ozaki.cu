@@ -354,21 +354,56 @@ __global__ void oz_exponent_kernel(OzView v, int* E) {
   }
 }
 
+// The same for views whose rows are contiguous (row stride 1): one thread per row,
+// 256 consecutive rows per block, so every K index reads 2 KB of consecutive memory
+// (the tiled kernel above reads 256 bytes per K index there, which wastes DRAM pages
+// when K is strided). Blocks split K into chunks; loads are unrolled four deep.
+constexpr int kER = 256;
+__global__ void __launch_bounds__(kER) oz_exponent_rows_kernel(OzView v, int* E, long kchunk) {
+  const long r = (long)blockIdx.y * kER + threadIdx.x;
+  const int batch = blockIdx.z, bh = batch / v.nblo, bl = batch % v.nblo;
+  const long Kt = (long)v.K * v.G;
+  const long k0 = (long)blockIdx.x * kchunk, k1 = k0 + kchunk < Kt ? k0 + kchunk : Kt;
+  if (r >= v.rows) return;
+  int em = kEmptyRow;
+  long k = k0;
+  for (; k + 4 <= k1; k += 4) {
+    long long b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) b[u] = __double_as_longlong(v.p[oz_offset(v, bh, bl, r, k + u)]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (b[u] & 0x7FFFFFFFFFFFFFFFll) em = max(em, exp_bits(b[u]));
+  }
+  for (; k < k1; ++k) {
+    const long long b = __double_as_longlong(v.p[oz_offset(v, bh, bl, r, k)]);
+    if (b & 0x7FFFFFFFFFFFFFFFll) em = max(em, exp_bits(b));
+  }
+  if (em > kEmptyRow) atomicMax(&E[(long)batch * v.rows + r], em);
+}
+
 // Slice s of 2^-E[row] entry, written tiled: element (batch, row, k) of slice s at
 // ((((batch nrt + row / TR) nkb + k / 64) 6 + s) TR + row % TR) 64 + k % 64, zero for
 // k >= K G and for the padding rows of the last tile. The entry becomes the integer
 // F = round(|x| 2^(47-E)) (|F| < 2^47, from the bits of x, rounding half up), signed,
 // then balanced base-256 digits from the bottom: n_6 .. n_2 in [-128, 127], n_1 = the
 // rest (|n_1| <= 128), F = sum_s n_s 2^(8(6-s)).
-__global__ void oz_slice_kernel(OzView v, const int* E, __nv_bfloat16* S, long Kpad, int TR, int nrt) {
-  __shared__ long long t[kT][kT + 1];
+// One block per 64 x 64 tile (64 rows, one 64-wide K block), 64 x 4 threads: the
+// operand is read along its unit-stride direction (512 bytes per warp pair) and every
+// output row of every slice is written as one full 128-byte line.
+constexpr int kST = 64;
+__global__ void __launch_bounds__(256) oz_slice_kernel(OzView v, const int* E, __nv_bfloat16* S, long Kpad, int TR,
+                                                       int nrt) {
+  __shared__ long long t[kST][kST + 1];  // [row][k]
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const long r0 = (long)blockIdx.y * kT, k0 = (long)blockIdx.x * kT;
+  const long r0 = (long)blockIdx.y * kST, k0 = (long)blockIdx.x * kST;
   const int batch = blockIdx.z, bh = batch / v.nblo, bl = batch % v.nblo;
   const long Kt = (long)v.K * v.G;
   const long nkb = Kpad / 64;
   const bool kfast = (v.sK == 1 && v.sR != 1);
-  for (int i = ty; i < kT; i += 8) {
+#pragma unroll 4
+  for (int j = 0; j < kST / 4; ++j) {
+    const int i = ty + 4 * j;
     const long r = kfast ? r0 + i : r0 + tx, k = kfast ? k0 + tx : k0 + i;
     long long b = 0;
     if (r < v.rows && k < Kt) b = __double_as_longlong(v.p[oz_offset(v, bh, bl, r, k)]);
@@ -376,10 +411,12 @@ __global__ void oz_slice_kernel(OzView v, const int* E, __nv_bfloat16* S, long K
     else t[tx][i] = b;
   }
   __syncthreads();
-  for (int i = ty; i < kT; i += 8) {
-    const long r = r0 + i, k = k0 + tx;
+  const long k = k0 + tx;
+#pragma unroll 2
+  for (int j = 0; j < kST / 4; ++j) {
+    const long r = r0 + ty + 4 * j;
     if (r >= (long)nrt * TR || k >= Kpad) continue;
-    const long long b = t[i][tx];
+    const long long b = t[ty + 4 * j][tx];
     const int e = r < v.rows ? E[(long)batch * v.rows + r] : kEmptyRow;
     long long F = 0;
     if ((b & 0x7FFFFFFFFFFFFFFFll) && e != kEmptyRow) {
@@ -433,14 +470,23 @@ void ozaki_slice(attn_ctx* ctx, const OzView& v, long Kpad, int tile_rows, DevBu
   const long rt = (v.rows + kT - 1) / kT;
   ATTN_REQUIRE(rt <= 65535, ATTN_EUNSUPPORTED, "too many rows for the split GEMM");
   dim3 blk(kT, 8);
-  // exponent pass: k tiles folded so that the grid stays modest
-  const long kt = (Kt + kT - 1) / kT;
-  dim3 ge((unsigned)std::min<long>(kt, std::max<long>(1, 8192 / std::max<long>(rt * nb, 1))), (unsigned)rt,
-          (unsigned)nb);
-  oz_exponent_kernel<<<ge, blk, 0, st>>>(v, exps.as<int>());
-  dim3 gs((unsigned)((Kpad + kT - 1) / kT), (unsigned)((padded + kT - 1) / kT), (unsigned)nb);
-  ATTN_REQUIRE(gs.x <= 2147483647u, ATTN_EUNSUPPORTED, "K too large for the split GEMM");
-  oz_slice_kernel<<<gs, blk, 0, st>>>(v, exps.as<int>(), slices.as<__nv_bfloat16>(), Kpad, tile_rows, nrt);
+  if (v.sR == 1) {
+    // rows contiguous: one thread per row, K split into chunks for about 2048 blocks
+    const long rb = (v.rows + kER - 1) / kER;
+    const long nchunk = std::max<long>(1, std::min<long>((Kt + 63) / 64, 2048 / std::max<long>(rb * nb, 1)));
+    const long kchunk = (Kt + nchunk - 1) / nchunk;
+    dim3 ge((unsigned)((Kt + kchunk - 1) / kchunk), (unsigned)rb, (unsigned)nb);
+    oz_exponent_rows_kernel<<<ge, kER, 0, st>>>(v, exps.as<int>(), kchunk);
+  } else {
+    // exponent pass: k tiles folded so that the grid stays modest
+    const long kt = (Kt + kT - 1) / kT;
+    dim3 ge((unsigned)std::min<long>(kt, std::max<long>(1, 8192 / std::max<long>(rt * nb, 1))), (unsigned)rt,
+            (unsigned)nb);
+    oz_exponent_kernel<<<ge, blk, 0, st>>>(v, exps.as<int>());
+  }
+  dim3 gs((unsigned)(Kpad / kST), (unsigned)((padded + kST - 1) / kST), (unsigned)nb);
+  ATTN_REQUIRE(gs.y <= 65535, ATTN_EUNSUPPORTED, "too many rows for the split GEMM");
+  oz_slice_kernel<<<gs, dim3(kST, 4), 0, st>>>(v, exps.as<int>(), slices.as<__nv_bfloat16>(), Kpad, tile_rows, nrt);
   ctx->launches += 3;
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
