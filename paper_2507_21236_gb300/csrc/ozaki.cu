@@ -29,8 +29,11 @@
 // with 2^E_i and 2^E_j at most twice the largest |entry| of row i of P and of
 // row j of Q. K per launch is limited to 65536 so the int64 sum cannot overflow.
 //
-// Kernel: one CTA per 128 x 64 output tile of one batch entry. Warp 0 is the
-// TMA producer; warps 1 and 2 issue the MMAs, each for its own set of diagonals
+// Kernel: persistent, one CTA per SM walking the 128 x 64 output tiles of every
+// batch entry (tile t = blockIdx.x + i gridDim.x, column tiles fastest so that CTAs
+// running at the same time share the P tile in L2); barriers and tensor memory are
+// set up once, and the copies and MMAs of the next tile overlap the epilogue of the
+// current one. Warp 0 is the TMA producer; warps 1 and 2 issue the MMAs, each for its own set of diagonals
 // (an MMA costs its issuing thread about as long as the tensor pipe takes for an
 // N = 64 tile, so one thread cannot keep the pipe busy); warps 3-18 read the
 // diagonals (four warps per 32-lane quarter w % 4, 16 columns each). A diagonal is
@@ -40,6 +43,7 @@
 // waits are bounded; on a timeout the CTA records an error code, stops issuing,
 // drains its copies and frees TMEM.
 #include <algorithm>
+#include <cmath>
 
 #include "ozaki.h"
 #include "tc_ptx.h"
@@ -77,8 +81,9 @@ struct OzParams {
   const int* EQ;           // [batches of Q][N]
   double* C;
   long c_rs, c_cs, c_bhi, c_blo;
-  double alpha, beta;
-  long batch_offset;
+  double alpha_rest, beta;  // alpha = alpha_rest 2^alpha_exp (alpha_rest = 1 for a power of two)
+  int alpha_exp;
+  long tiles;              // column tiles x row tiles x batch entries
   int* err;
 };
 
@@ -88,6 +93,34 @@ struct OzParams {
 struct OzMaps {
   CUtensorMap p, q;  // [((batch * nrt + tile) * nkb + kb) * 6 + s][tile rows][64], boxes {64, 128 / 64, 1}
 };
+
+// a 2^e as a double for an int64 a, rounded to nearest even like ldexp((double)a, e),
+// from integer instructions alone (this GPU issues about two FP64 operations per SM
+// and cycle, which made the FP64 conversion the epilogue's bottleneck); the rare
+// results outside the normal range take the FP64 route.
+__device__ __forceinline__ double scaled_i64(long long a, int e) {
+  if (a == 0) return 0.0;
+  const unsigned long long sign = a < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long u = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  int top = 63 - __clzll(u);  // u in [2^top, 2^(top + 1))
+  unsigned long long m;
+  if (top > 52) {
+    const int sh = top - 52;
+    const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    m = u >> sh;
+    if (rem > half || (rem == half && (m & 1ull))) {
+      if (++m == (1ull << 53)) {
+        m >>= 1;
+        ++top;
+      }
+    }
+  } else {
+    m = u << (52 - top);
+  }
+  const int be = top + e + 1023;
+  if (be < 1 || be > 2046) return ldexp((double)a, e);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
 
 __device__ __forceinline__ bool window_end(int d, int kb, int nkb) {
   return (kb + 1) % kFold[d] == 0 || kb == nkb - 1;
@@ -116,11 +149,24 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto bar = [&](int i) { return sBar + 8u * (uint32_t)i; };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long b = (long)blockIdx.z + p.batch_offset;
-  const int bhi = (int)(b / p.Blo), blo = (int)(b % p.Blo);
-  const int bp = bhi * p.p_hi + blo * p.p_lo, bq = bhi * p.q_hi + blo * p.q_lo;
-  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * kQRows;
   const int nkb = p.nkb;
+  const int ntn = (p.N + kQRows - 1) / kQRows, ntm = (p.M + 127) / 128;
+  // tile t: column tile, row tile, batch entry (bhi, blo) and the operands' batch indices
+  struct Tile {
+    int nt, mt, bhi, blo, bp, bq;
+  };
+  auto tile = [&](long t) {
+    Tile r;
+    r.nt = (int)(t % ntn);
+    const long rest = t / ntn;
+    r.mt = (int)(rest % ntm);
+    const long b = rest / ntm;
+    r.bhi = (int)(b / p.Blo);
+    r.blo = (int)(b % p.Blo);
+    r.bp = r.bhi * p.p_hi + r.blo * p.p_lo;
+    r.bq = r.bhi * p.q_hi + r.blo * p.q_lo;
+    return r;
+  };
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < 2; ++i) {
@@ -151,35 +197,42 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
   const uint32_t tmem = *tmem_slot;  // diagonal d = c - 2 in columns 64 d .. 64 d + 63
 
   if (warp == 0 && lane == 0) {
-    // ---- producer: per K block the six Q slices, then the six P slices
-    const int zP = (bp * p.nrtP + (int)blockIdx.y) * nkb * kSlices;
-    const int zQ = (bq * p.nrtQ + (int)blockIdx.x) * nkb * kSlices;
+    // ---- producer: per K block the six Q slices, then the six P slices; g counts the
+    // K blocks of all tiles of this CTA
     int pst = 0, pissued = 0;
     uint32_t pph = 0;
-    int qissued = 0;
+    int qissued = 0, g = 0;
     bool ok = true;
-    for (int kb = 0; ok && kb < nkb; ++kb) {
-      const int qb = kb & 1;
-      if (kb >= 2 && !mbar_wait(bar(QEMPTY + qb), ((kb >> 1) - 1) & 1, p.err, 61, abort_flag)) break;
-      mbar_expect_tx(bar(QFULL + qb), (uint32_t)kQBufBytes);
-      for (int s = 0; s < kSlices; ++s)
-        tma_load_3d(sQ + qb * kQBufBytes + s * kQBytes, &maps.q, 0, 0, zQ + kb * kSlices + s, bar(QFULL + qb));
-      qissued = kb + 1;
-      for (int s = 0; s < kSlices; ++s) {
-        if (pissued >= kPStages && !mbar_wait(bar(PEMPTY + pst), pph ^ 1u, p.err, 62, abort_flag)) {
+    for (long t = blockIdx.x; ok && t < p.tiles; t += gridDim.x) {
+      const Tile tl = tile(t);
+      const int zP = (tl.bp * p.nrtP + tl.mt) * nkb * kSlices;
+      const int zQ = (tl.bq * p.nrtQ + tl.nt) * nkb * kSlices;
+      for (int kb = 0; ok && kb < nkb; ++kb, ++g) {
+        const int qb = g & 1;
+        if (g >= 2 && !mbar_wait(bar(QEMPTY + qb), ((g >> 1) - 1) & 1, p.err, 61, abort_flag)) {
           ok = false;
           break;
         }
-        mbar_expect_tx(bar(PFULL + pst), (uint32_t)kPBytes);
-        tma_load_3d(sP + pst * kPBytes, &maps.p, 0, 0, zP + kb * kSlices + s, bar(PFULL + pst));
-        ++pissued;
-        if (++pst == kPStages) { pst = 0; pph ^= 1u; }
+        mbar_expect_tx(bar(QFULL + qb), (uint32_t)kQBufBytes);
+        for (int s = 0; s < kSlices; ++s)
+          tma_load_3d(sQ + qb * kQBufBytes + s * kQBytes, &maps.q, 0, 0, zQ + kb * kSlices + s, bar(QFULL + qb));
+        qissued = g + 1;
+        for (int s = 0; s < kSlices; ++s) {
+          if (pissued >= kPStages && !mbar_wait(bar(PEMPTY + pst), pph ^ 1u, p.err, 62, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(bar(PFULL + pst), (uint32_t)kPBytes);
+          tma_load_3d(sP + pst * kPBytes, &maps.p, 0, 0, zP + kb * kSlices + s, bar(PFULL + pst));
+          ++pissued;
+          if (++pst == kPStages) { pst = 0; pph ^= 1u; }
+        }
       }
     }
     // drain: every issued copy must land before the CTA exits
-    for (int kb = (qissued > 2 ? qissued - 2 : 0); kb < qissued; ++kb) {
+    for (int q = (qissued > 2 ? qissued - 2 : 0); q < qissued; ++q) {
       long long t0 = clock64();
-      while (!mbar_try_wait(bar(QFULL + (kb & 1)), (kb >> 1) & 1) && clock64() - t0 < kWaitCycles) {}
+      while (!mbar_try_wait(bar(QFULL + (q & 1)), (q >> 1) & 1) && clock64() - t0 < kWaitCycles) {}
     }
     for (int q = (pissued > kPStages ? pissued - kPStages : 0); q < pissued; ++q) {
       long long t0 = clock64();
@@ -192,40 +245,49 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
     const uint32_t mine = me == 0 ? kIssuer0Diags : kIssuer1Diags;
     const uint32_t id = idesc_bf16(128, kQRows);
     const uint64_t dP0 = sw128_desc(sP), dQ0 = sw128_desc(sQ);
-    int pst = 0;
+    int pst = 0, g = 0;
     uint32_t pph = 0;
+    int windows[kDiags] = {0, 0, 0, 0, 0, 0};  // windows of diagonal d issued so far (all tiles)
     bool ok = true;
-    for (int kb = 0; ok && kb < nkb; ++kb) {
-      const int qb = kb & 1;
-      if (!mbar_wait(bar(QFULL + qb), (kb >> 1) & 1, p.err, 64, abort_flag)) break;
-      fence_after();
-      uint32_t touched = 0;
-      for (int s = 0; s < kSlices; ++s) {
-        if (!mbar_wait(bar(PFULL + pst), pph, p.err, 65, abort_flag)) { ok = false; break; }
-        fence_after();
-        const uint64_t dP = dP0 + (uint64_t)(pst * (kPBytes >> 4));
-        for (int t = 0; s + t < kDiags; ++t) {
-          const int d = s + t;
-          if (!((mine >> d) & 1u)) continue;
-          const bool first = (kb % kFold[d] == 0) && !((touched >> d) & 1u);
-          // a new window reuses the diagonal's accumulator once the epilogue has read the last one
-          if (first && kb > 0 &&
-              !mbar_wait(bar(DEMPTY + d), (kb / kFold[d] - 1) & 1, p.err, 63, abort_flag)) {
-            ok = false;
-            break;
-          }
-          const uint64_t dQ = dQ0 + (uint64_t)((qb * kQBufBytes + t * kQBytes) >> 4);
-          mma4_ss(tmem + 64u * (uint32_t)d, dP, dQ, id, first ? 0u : 1u);
-          touched |= 1u << d;
+    for (long tt = blockIdx.x; ok && tt < p.tiles; tt += gridDim.x) {
+      for (int kb = 0; ok && kb < nkb; ++kb, ++g) {
+        const int qb = g & 1;
+        if (!mbar_wait(bar(QFULL + qb), (g >> 1) & 1, p.err, 64, abort_flag)) {
+          ok = false;
+          break;
         }
-        mma_commit(bar(PEMPTY + pst));
-        if (++pst == kPStages) { pst = 0; pph ^= 1u; }
+        fence_after();
+        uint32_t touched = 0;
+        for (int s = 0; s < kSlices; ++s) {
+          if (!mbar_wait(bar(PFULL + pst), pph, p.err, 65, abort_flag)) { ok = false; break; }
+          fence_after();
+          const uint64_t dP = dP0 + (uint64_t)(pst * (kPBytes >> 4));
+          for (int t = 0; s + t < kDiags; ++t) {
+            const int d = s + t;
+            if (!((mine >> d) & 1u)) continue;
+            const bool first = (kb % kFold[d] == 0) && !((touched >> d) & 1u);
+            // a new window reuses the diagonal's accumulator once the epilogue has read the last one
+            if (first && windows[d] > 0 &&
+                !mbar_wait(bar(DEMPTY + d), (windows[d] - 1) & 1, p.err, 63, abort_flag)) {
+              ok = false;
+              break;
+            }
+            const uint64_t dQ = dQ0 + (uint64_t)((qb * kQBufBytes + t * kQBytes) >> 4);
+            mma4_ss(tmem + 64u * (uint32_t)d, dP, dQ, id, first ? 0u : 1u);
+            touched |= 1u << d;
+          }
+          mma_commit(bar(PEMPTY + pst));
+          if (++pst == kPStages) { pst = 0; pph ^= 1u; }
+          if (!ok) break;
+        }
+        mma_commit(bar(QEMPTY + qb));
         if (!ok) break;
+        for (int d = 0; d < kDiags; ++d)
+          if (((mine >> d) & 1u) && window_end(d, kb, nkb)) {
+            mma_commit(bar(DFULL + d));
+            ++windows[d];
+          }
       }
-      mma_commit(bar(QEMPTY + qb));
-      if (!ok) break;
-      for (int d = 0; d < kDiags; ++d)
-        if (((mine >> d) & 1u) && window_end(d, kb, nkb)) mma_commit(bar(DFULL + d));
     }
     mma_commit(bar(MDONE + me));
     long long t0 = clock64();
@@ -235,45 +297,53 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
     // finished window of a diagonal is folded into an int64 fixed-point sum
     const int q4 = warp & 3, h = (warp - 3) >> 2;
     const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
-    long long acc[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = 0;
+    int windows[kDiags] = {0, 0, 0, 0, 0, 0};  // windows of diagonal d read so far (all tiles)
     bool ok = true;
-    for (int kb = 0; ok && kb < nkb; ++kb) {
+    for (long tt = blockIdx.x; ok && tt < p.tiles; tt += gridDim.x) {
+      long long acc[16];
 #pragma unroll
-      for (int d = 0; d < kDiags; ++d) {
-        if (!window_end(d, kb, nkb)) continue;
-        // warp-uniform: the TMEM loads below are .sync.aligned
-        if (!__all_sync(0xffffffffu, mbar_wait(bar(DFULL + d), (kb / kFold[d]) & 1, p.err, 66, abort_flag))) {
-          ok = false;
-          break;
-        }
-        fence_after();
-        float v[16];
-        tmem_ld16(tmem + lane_off + 64u * (uint32_t)d + 16u * (uint32_t)h, v);
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar(DEMPTY + d));
+      for (int c = 0; c < 16; ++c) acc[c] = 0;
+      for (int kb = 0; ok && kb < nkb; ++kb) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const long long x = (long long)__float2int_rn(v[c]);  // exact: |v| <= 2^24
-          if (d < kDiags - 1) acc[c] += x << (8 * (kDiags - 2 - d));
-          else acc[c] += (x + 128) >> 8;  // the finest diagonal, rounded to the unit
+        for (int d = 0; d < kDiags; ++d) {
+          if (!window_end(d, kb, nkb)) continue;
+          // warp-uniform: the TMEM loads below are .sync.aligned
+          if (!__all_sync(0xffffffffu, mbar_wait(bar(DFULL + d), windows[d] & 1, p.err, 66, abort_flag))) {
+            ok = false;
+            break;
+          }
+          ++windows[d];
+          fence_after();
+          float v[16];
+          tmem_ld16(tmem + lane_off + 64u * (uint32_t)d + 16u * (uint32_t)h, v);
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(DEMPTY + d));
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const long long x = (long long)__float2int_rn(v[c]);  // exact: |v| <= 2^24
+            if (d < kDiags - 1) acc[c] += x << (8 * (kDiags - 2 - d));
+            else acc[c] += (x + 128) >> 8;  // the finest diagonal, rounded to the unit
+          }
         }
       }
-    }
-    const int i = m0 + q4 * 32 + lane;
-    if (ok && i < p.M) {
-      const int ep = p.EP[(long)bp * p.M + i];
-      const long cbase = (long)bhi * p.c_bhi + (long)blo * p.c_blo + (long)i * p.c_rs;
+      const Tile tl = tile(tt);
+      const int i = tl.mt * 128 + q4 * 32 + lane;
+      if (ok && i < p.M) {
+        const int ep = p.EP[(long)tl.bp * p.M + i];
+        const long cbase = (long)tl.bhi * p.c_bhi + (long)tl.blo * p.c_blo + (long)i * p.c_rs;
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int j = n0 + 16 * h + c;
-        if (j < p.N) {
-          const int e = ep + p.EQ[(long)bq * p.N + j] - kUnitExp;
-          const double v = p.alpha * ldexp((double)acc[c], e);
-          double* cp = p.C + cbase + (long)j * p.c_cs;
-          *cp = (p.beta == 0.0) ? v : fma(p.beta, *cp, v);
+        for (int c = 0; c < 16; ++c) {
+          const int j = tl.nt * kQRows + 16 * h + c;
+          if (j < p.N) {
+            const int e = ep + p.EQ[(long)tl.bq * p.N + j] - kUnitExp + p.alpha_exp;
+            double v = scaled_i64(acc[c], e);
+            if (p.alpha_rest != 1.0) v *= p.alpha_rest;
+            double* cp = p.C + cbase + (long)j * p.c_cs;
+            if (p.beta == 0.0) *cp = v;
+            else if (p.beta == 1.0) *cp += v;
+            else *cp = fma(p.beta, *cp, v);
+          }
         }
       }
     }
@@ -451,7 +521,6 @@ void encode_slices(CUtensorMap* map, const __nv_bfloat16* p, int tile_rows, long
   ATTN_REQUIRE(r == CUDA_SUCCESS, ATTN_ECUDA, "cuTensorMapEncodeTiled failed for Ozaki slices");
 }
 
-int grid_cap(long n) { return (int)std::max<long>(1, std::min<long>(n, 65535)); }
 
 }  // namespace
 
@@ -559,18 +628,20 @@ void gemm_f64_ozaki(attn_ctx* ctx, const GemmF64& g0) {
     prm.EP = ctx->oz_ws[1].as<int>();
     prm.EQ = ctx->oz_ws[3].as<int>();
     prm.C = g0.C; prm.c_rs = c_rs; prm.c_cs = c_cs; prm.c_bhi = g0.cBhi; prm.c_blo = g0.cBlo;
-    prm.alpha = g0.alpha;
+    {
+      int ex = 0;
+      const double fr = std::frexp(g0.alpha, &ex);  // alpha = fr 2^ex, fr in [0.5, 1)
+      const bool pow2 = std::isfinite(g0.alpha) && std::fabs(fr) == 0.5;
+      prm.alpha_exp = pow2 ? ex - 1 : 0;
+      prm.alpha_rest = pow2 ? (fr < 0 ? -1.0 : 1.0) : g0.alpha;
+    }
     prm.beta = ga == 0 ? g0.beta : 1.0;
     prm.err = ctx->oz_err.as<int>();
-    const long total = (long)g0.Bhi * g0.Blo;
-    dim3 grid((unsigned)((N + kQRows - 1) / kQRows), (unsigned)((M + 127) / 128), 1);
-    ATTN_REQUIRE(grid.y <= 65535, ATTN_EUNSUPPORTED, "M too large for the split GEMM");
-    for (long off = 0; off < total; off += 65535) {
-      grid.z = (unsigned)grid_cap(total - off);
-      prm.batch_offset = off;
-      ozaki_gemm_kernel<<<grid, kOzThreads, smem, ctx->stream>>>(maps, prm);
-      ctx->launches++;
-    }
+    // persistent: one CTA per SM (the shared-memory ring allows one), at most one per tile
+    prm.tiles = (long)((N + kQRows - 1) / kQRows) * ((M + 127) / 128) * g0.Bhi * g0.Blo;
+    const int grid = (int)std::min<long>(prm.tiles, std::max(ctx->num_sms, 1));
+    ozaki_gemm_kernel<<<grid, kOzThreads, smem, ctx->stream>>>(maps, prm);
+    ctx->launches++;
   }
   ctx->prof_end(3, fl);
   ATTN_CHECK_CUDA(cudaGetLastError());
