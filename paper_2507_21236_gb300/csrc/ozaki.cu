@@ -17,13 +17,13 @@
 //    2^-46 of the row scales) are multiplied on the tensor cores. Pairs on
 //    one diagonal c = s + t share the scale 2^(2-8c) and accumulate into one
 //    TMEM accumulator. Every product is an integer of magnitude at most 2^14;
-//  * diagonal d sums d + 1 slice pairs, so it can accumulate several K blocks in
-//    TMEM before its partial sums could leave the exact FP32 range: 16, 8, 5, 3,
-//    3 and 2 blocks of 64 for d = 0 .. 5 keep them at or below 2^24. At the end of
-//    each such window the epilogue folds the diagonal into an int64 fixed-point
-//    sum per output element (unit 2^-46 of the row scales; the finest diagonal is
-//    rounded to that unit) while the MMAs of the other diagonals go on, and the
-//    sum is converted to FP64 once.
+//  * diagonal d (0-based, d = s + t - 2) sums d + 1 slice pairs, so over F K
+//    blocks of 64 its partial sums stay below (d + 1) 2^14 64 F, exact in FP32
+//    while (d + 1) F <= 16. Diagonals 0-3 accumulate over windows of 4 K blocks,
+//    diagonals 4 and 5 over windows of 2. At the end of each window the epilogue
+//    folds the diagonals into an int64 fixed-point sum per output element (unit
+//    2^-46 of the row scales; the finest diagonal is rounded to that unit), and
+//    the sum is converted to FP64 once.
 //
 // The error is normwise: |C - C~|_ij <= about (K + 2) 2^-46 2^(E_i + E_j),
 // with 2^E_i and 2^E_j at most twice the largest |entry| of row i of P and of
@@ -33,15 +33,26 @@
 // batch entry (tile t = blockIdx.x + i gridDim.x, column tiles fastest so that CTAs
 // running at the same time share the P tile in L2); barriers and tensor memory are
 // set up once, and the copies and MMAs of the next tile overlap the epilogue of the
-// current one. Warp 0 is the TMA producer; warps 1 and 2 issue the MMAs, each for its own set of diagonals
-// (an MMA costs its issuing thread about as long as the tensor pipe takes for an
-// N = 64 tile, so one thread cannot keep the pipe busy); warps 3-18 read the
-// diagonals (four warps per 32-lane quarter w % 4, 16 columns each). A diagonal is
-// handed back to its issuer as soon as it has been read, so the epilogue of one
-// window overlaps the MMAs of the next. The six Q slices of a K block (48 KB) are
-// double-buffered; the P slices stream through a ring of eight 16 KB stages. All
-// waits are bounded; on a timeout the CTA records an error code, stops issuing,
-// drains its copies and frees TMEM.
+// current one. Warp 0 is the TMA producer, warps 1 and 2 issue the MMAs, warps
+// 3-18 read the accumulators (four warps per 32-lane quarter w % 4, 16 columns
+// each).
+//
+// Wide MMAs. A thread can issue a tcgen05.mma only about every 70-110 cycles
+// whatever its N, while an M = 128, K = 16 MMA runs N / 2 cycles, so pair-by-pair
+// N = 64 products would leave the tensor pipe idle more than half of the time. The
+// six Q slices of a K block sit one after another in shared memory and the six
+// diagonal accumulators one after another in tensor memory, so one MMA of width
+// 64 n multiplies P slice s with Q slices t .. t + n - 1 into diagonals s + t ..
+// s + t + n - 1 at once: warp 1 covers diagonals 0-3 with one MMA per P slice
+// s <= 3 (N = 256 - 64 s), warp 2 diagonals 4-5 with one per P slice (N = 128,
+// and 64 for s = 5): 10 MMAs per K step instead of 21. Each issuer owns its
+// diagonals, so the MMA that restarts a window precedes every other write to them.
+// Diagonals 4-5 have two accumulator buffers (6 x 64 + 2 x 64 = 512 columns) and
+// alternate between them from window to window, so the epilogue reads one while
+// the MMAs fill the other; diagonals 0-3 are handed back as soon as they are read.
+// The six Q slices of a K block (48 KB) are double-buffered; the P slices stream
+// through a ring of eight 16 KB stages. All waits are bounded; on a timeout the CTA
+// records an error code, stops issuing, drains its copies and frees TMEM.
 #include <algorithm>
 #include <cmath>
 
@@ -64,13 +75,9 @@ constexpr int kPStages = 8;
 constexpr int kQBufBytes = kSlices * kQBytes;
 constexpr int kEmptyRow = -2000;        // exponent of an all-zero row
 constexpr int kUnitExp = 46;            // fixed-point unit 2^-46 of the row scales
-// K blocks diagonal d accumulates in TMEM before the epilogue folds it: diagonal d
-// sums d + 1 slice pairs of products below 2^14 in magnitude, so over F_d blocks of
-// 64 its partial sums stay below (d + 1) 2^14 64 F_d <= 2^24 and FP32 holds them
-// exactly (16, 8, 5, 3, 3, 2 blocks for d = 0 .. 5).
-__device__ __constant__ int kFold[kDiags] = {16, 8, 5, 3, 3, 2};
-// The two MMA issuers own complementary diagonal sets (11 and 10 slice pairs).
-constexpr uint32_t kIssuer0Diags = (1u << 0) | (1u << 3) | (1u << 5), kIssuer1Diags = (1u << 1) | (1u << 2) | (1u << 4);
+// K blocks per accumulation window: diagonals 0-3 (one TMEM buffer, columns 64 d)
+// and diagonals 4-5 (two buffers, columns 256 + 128 b + 64 (d - 4))
+constexpr int kFoldA = 4, kFoldB = 2;
 
 struct OzParams {
   int M, N, nkb;           // rows of P, rows of Q, 64-wide K blocks
@@ -122,8 +129,8 @@ __device__ __forceinline__ double scaled_i64(long long a, int e) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
-__device__ __forceinline__ bool window_end(int d, int kb, int nkb) {
-  return (kb + 1) % kFold[d] == 0 || kb == nkb - 1;
+__device__ __forceinline__ bool window_end(int fold, int kb, int nkb) {
+  return (kb + 1) % fold == 0 || kb == nkb - 1;
 }
 
 __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_constant__ OzMaps maps, OzParams p) {
@@ -139,9 +146,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
     QEMPTY = 2,                 // both issuers release a Q buffer
     PFULL = 4,
     PEMPTY = 4 + kPStages,      // both issuers release a P stage
-    DFULL = 4 + 2 * kPStages,   // [d]: a window of diagonal d is complete in TMEM
-    DEMPTY = DFULL + kDiags,    // [d]: the epilogue has read it
-    MDONE = DEMPTY + kDiags,    // [issuer]: every MMA of that issuer has completed
+    AFULL = 4 + 2 * kPStages,   // a window of diagonals 0-3 is complete in TMEM
+    AEMPTY = AFULL + 1,         // the epilogue has read it
+    BFULL = AEMPTY + 1,         // [b]: a window of diagonals 4-5 is complete in buffer b
+    BEMPTY = BFULL + 2,         // [b]: the epilogue has read buffer b
+    MDONE = BEMPTY + 2,         // [issuer]: every MMA of that issuer has completed
     NBAR = MDONE + 2
   };
   uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + (sBar - base));
@@ -178,9 +187,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
       mbar_init(bar(PFULL + i), 1);
       mbar_init(bar(PEMPTY + i), 2);
     }
-    for (int d = 0; d < kDiags; ++d) {
-      mbar_init(bar(DFULL + d), 1);
-      mbar_init(bar(DEMPTY + d), 16);
+    mbar_init(bar(AFULL), 1);
+    mbar_init(bar(AEMPTY), 16);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(bar(BFULL + i), 1);
+      mbar_init(bar(BEMPTY + i), 16);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -194,7 +205,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t tmem = *tmem_slot;  // diagonal d = c - 2 in columns 64 d .. 64 d + 63
+  const uint32_t tmem = *tmem_slot;  // diagonals 0-3 at columns 64 d, 4-5 at 256 + 128 b + 64 (d - 4)
 
   if (warp == 0 && lane == 0) {
     // ---- producer: per K block the six Q slices, then the six P slices; g counts the
@@ -242,12 +253,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
     // ---- MMA issue, one thread per diagonal set: diagonal d accumulates the pairs
     // (s, t) with s + t = d (0-based slices) over a window of kFold[d] K blocks
     const int me = warp - 1;
-    const uint32_t mine = me == 0 ? kIssuer0Diags : kIssuer1Diags;
-    const uint32_t id = idesc_bf16(128, kQRows);
     const uint64_t dP0 = sw128_desc(sP), dQ0 = sw128_desc(sQ);
+    const int fold = me == 0 ? kFoldA : kFoldB;
     int pst = 0, g = 0;
     uint32_t pph = 0;
-    int windows[kDiags] = {0, 0, 0, 0, 0, 0};  // windows of diagonal d issued so far (all tiles)
+    int win = 0;  // windows of this issuer's diagonals begun so far (all tiles)
     bool ok = true;
     for (long tt = blockIdx.x; ok && tt < p.tiles; tt += gridDim.x) {
       for (int kb = 0; ok && kb < nkb; ++kb, ++g) {
@@ -257,36 +267,45 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
           break;
         }
         fence_after();
-        uint32_t touched = 0;
+        const bool first = kb % fold == 0;
+        // a window refills its accumulator once the epilogue has read what the last
+        // window left there: window win - 1 (diagonals 0-3) or win - 2 (4-5, two buffers)
+        if (first && me == 0 && win > 0 && !mbar_wait(bar(AEMPTY), (win - 1) & 1, p.err, 63, abort_flag)) {
+          ok = false;
+          break;
+        }
+        if (first && me == 1 && win > 1 &&
+            !mbar_wait(bar(BEMPTY + (win & 1)), ((win >> 1) - 1) & 1, p.err, 63, abort_flag)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t accB = tmem + 256u + 128u * (uint32_t)(win & 1);
         for (int s = 0; s < kSlices; ++s) {
           if (!mbar_wait(bar(PFULL + pst), pph, p.err, 65, abort_flag)) { ok = false; break; }
           fence_after();
           const uint64_t dP = dP0 + (uint64_t)(pst * (kPBytes >> 4));
-          for (int t = 0; s + t < kDiags; ++t) {
-            const int d = s + t;
-            if (!((mine >> d) & 1u)) continue;
-            const bool first = (kb % kFold[d] == 0) && !((touched >> d) & 1u);
-            // a new window reuses the diagonal's accumulator once the epilogue has read the last one
-            if (first && windows[d] > 0 &&
-                !mbar_wait(bar(DEMPTY + d), (windows[d] - 1) & 1, p.err, 63, abort_flag)) {
-              ok = false;
-              break;
-            }
-            const uint64_t dQ = dQ0 + (uint64_t)((qb * kQBufBytes + t * kQBytes) >> 4);
-            mma4_ss(tmem + 64u * (uint32_t)d, dP, dQ, id, first ? 0u : 1u);
-            touched |= 1u << d;
+          const uint32_t restart = (first && s == 0) ? 0u : 1u;
+          if (me == 0) {
+            // diagonals s .. 3 from Q slices 0 .. 3 - s
+            if (s < 4)
+              mma4_ss(tmem + 64u * (uint32_t)s, dP, dQ0 + (uint64_t)((qb * kQBufBytes) >> 4),
+                      idesc_bf16(128, 64 * (4 - s)), restart);
+          } else {
+            // diagonals 4-5 from Q slices 4 - s, 5 - s (s <= 4); diagonal 5 from Q slice 0 (s = 5)
+            const int t0 = s < 5 ? 4 - s : 0;
+            mma4_ss(s < 5 ? accB : accB + 64u, dP, dQ0 + (uint64_t)((qb * kQBufBytes + t0 * kQBytes) >> 4),
+                    idesc_bf16(128, s < 5 ? 128 : 64), restart);
           }
           mma_commit(bar(PEMPTY + pst));
           if (++pst == kPStages) { pst = 0; pph ^= 1u; }
-          if (!ok) break;
         }
         mma_commit(bar(QEMPTY + qb));
         if (!ok) break;
-        for (int d = 0; d < kDiags; ++d)
-          if (((mine >> d) & 1u) && window_end(d, kb, nkb)) {
-            mma_commit(bar(DFULL + d));
-            ++windows[d];
-          }
+        if (window_end(fold, kb, nkb)) {
+          mma_commit(bar(me == 0 ? AFULL : BFULL + (win & 1)));
+          ++win;
+        }
       }
     }
     mma_commit(bar(MDONE + me));
@@ -297,33 +316,57 @@ __global__ void __launch_bounds__(kOzThreads, 1) ozaki_gemm_kernel(const __grid_
     // finished window of a diagonal is folded into an int64 fixed-point sum
     const int q4 = warp & 3, h = (warp - 3) >> 2;
     const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
-    int windows[kDiags] = {0, 0, 0, 0, 0, 0};  // windows of diagonal d read so far (all tiles)
+    int winA = 0, winB = 0;  // windows read so far (all tiles)
     bool ok = true;
     for (long tt = blockIdx.x; ok && tt < p.tiles; tt += gridDim.x) {
       long long acc[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) acc[c] = 0;
       for (int kb = 0; ok && kb < nkb; ++kb) {
-#pragma unroll
-        for (int d = 0; d < kDiags; ++d) {
-          if (!window_end(d, kb, nkb)) continue;
+        if (window_end(kFoldA, kb, nkb)) {
           // warp-uniform: the TMEM loads below are .sync.aligned
-          if (!__all_sync(0xffffffffu, mbar_wait(bar(DFULL + d), windows[d] & 1, p.err, 66, abort_flag))) {
+          if (!__all_sync(0xffffffffu, mbar_wait(bar(AFULL), winA & 1, p.err, 66, abort_flag))) {
             ok = false;
             break;
           }
-          ++windows[d];
+          ++winA;
           fence_after();
-          float v[16];
-          tmem_ld16(tmem + lane_off + 64u * (uint32_t)d + 16u * (uint32_t)h, v);
-          fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(bar(DEMPTY + d));
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const long long x = (long long)__float2int_rn(v[c]);  // exact: |v| <= 2^24
-            if (d < kDiags - 1) acc[c] += x << (8 * (kDiags - 2 - d));
-            else acc[c] += (x + 128) >> 8;  // the finest diagonal, rounded to the unit
+          for (int d = 0; d < 4; ++d) {
+            float v[16];
+            tmem_ld16(tmem + lane_off + 64u * (uint32_t)d + 16u * (uint32_t)h, v);
+            if (d == 3) {
+              fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(bar(AEMPTY));
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c)  // exact: |v| <= 2^24
+              acc[c] += (long long)__float2int_rn(v[c]) << (8 * (kDiags - 2 - d));
+          }
+        }
+        if (window_end(kFoldB, kb, nkb)) {
+          const int b = winB & 1;
+          if (!__all_sync(0xffffffffu, mbar_wait(bar(BFULL + b), (winB >> 1) & 1, p.err, 67, abort_flag))) {
+            ok = false;
+            break;
+          }
+          ++winB;
+          fence_after();
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            float v[16];
+            tmem_ld16(tmem + lane_off + 256u + 128u * (uint32_t)b + 64u * (uint32_t)e + 16u * (uint32_t)h, v);
+            if (e == 1) {
+              fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(bar(BEMPTY + b));
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const long long x = (long long)__float2int_rn(v[c]);
+              acc[c] += e == 0 ? x : (x + 128) >> 8;  // diagonal 4 is the unit; 5, the finest, rounded to it
+            }
           }
         }
       }
