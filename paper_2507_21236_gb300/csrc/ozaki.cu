@@ -524,31 +524,49 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(OzView v, const int* E, _
     else t[tx][i] = b;
   }
   __syncthreads();
-  const long k = k0 + tx;
-#pragma unroll 2
-  for (int j = 0; j < kST / 4; ++j) {
-    const long r = r0 + ty + 4 * j;
+  // each thread: one row and 8 consecutive k, every slice written as one 16-byte store
+  // (8 threads fill the 128-byte row of a slice block)
+  const int lin = ty * kST + tx;
+  const long sstride = (long)TR * 64;
+#pragma unroll 1
+  for (int rep = 0; rep < 2; ++rep) {
+    const int idx = lin + 256 * rep, i = idx >> 3, kq = (idx & 7) * 8;
+    const long r = r0 + i, k = k0 + kq;
     if (r >= (long)nrt * TR || k >= Kpad) continue;
-    const long long b = t[ty + 4 * j][tx];
     const int e = r < v.rows ? E[(long)batch * v.rows + r] : kEmptyRow;
-    long long F = 0;
-    if ((b & 0x7FFFFFFFFFFFFFFFll) && e != kEmptyRow) {
-      const int ef = (int)((b >> 52) & 0x7FF);
-      const long long mant = (b & 0xFFFFFFFFFFFFFll) | (ef ? (1ll << 52) : 0ll);
-      const int sh = (ef ? ef - 1075 : -1074) + 47 - e;  // |x| = mant 2^(ef - 1075)
-      if (sh >= 0) F = mant << sh;                       // < 2^47 since |x| < 2^e
-      else if (sh > -64) F = (sh == -63 ? 0ll : (mant + (1ll << (-sh - 1))) >> (-sh));
-      if (b < 0) F = -F;
-    }
-    __nv_bfloat16* out = S + ((((long)batch * nrt + r / TR) * nkb + (k >> 6)) * kSlices * TR + r % TR) * 64 + (k & 63);
-    const long sstride = (long)TR * 64;
+    uint32_t w[kSlices][4];
 #pragma unroll
-    for (int sl = kSlices - 1; sl >= 1; --sl) {
-      const int d = (int)(((F & 255) ^ 128) - 128);  // balanced digit in [-128, 127]
-      out[(long)sl * sstride] = __int2bfloat16_rn(d);  // exact: |d| <= 128
-      F = (F - d) >> 8;
+    for (int u = 0; u < 8; ++u) {
+      const long long b = t[i][kq + u];
+      long long F = 0;
+      if ((b & 0x7FFFFFFFFFFFFFFFll) && e != kEmptyRow) {
+        const int ef = (int)((b >> 52) & 0x7FF);
+        const long long mant = (b & 0xFFFFFFFFFFFFFll) | (ef ? (1ll << 52) : 0ll);
+        const int sh = (ef ? ef - 1075 : -1074) + 47 - e;  // |x| = mant 2^(ef - 1075)
+        if (sh >= 0) F = mant << sh;                       // < 2^47 since |x| < 2^e
+        else if (sh > -64) F = (sh == -63 ? 0ll : (mant + (1ll << (-sh - 1))) >> (-sh));
+        if (b < 0) F = -F;
+      }
+      // Balanced base-256 digits: the bytes of G = F + 128 (1 + 2^8 + ... + 2^32) minus
+      // 128 are the digits n_6 .. n_2 in [-128, 127], and G >> 40 is n_1 (|n_1| <= 128),
+      // the same digits as peeling F from the bottom. A digit g - 128 becomes a float
+      // exactly as (2^23 + g) - (2^23 + 128), and a BF16 as the float's upper half.
+      const long long G = F + 0x8080808080ll;
+      const uint32_t lo = (uint32_t)G, hi = (uint32_t)(G >> 32);
+      const uint32_t g[kSlices] = {(uint32_t)(((int)hi >> 8) + 128), hi & 255u, lo >> 24, (lo >> 16) & 255u,
+                                   (lo >> 8) & 255u, lo & 255u};
+#pragma unroll
+      for (int sl = 0; sl < kSlices; ++sl) {
+        const uint32_t f = __float_as_uint(__uint_as_float(0x4B000000u + g[sl]) - 8388736.0f);
+        if (u & 1) w[sl][u >> 1] = __byte_perm(w[sl][u >> 1], f, 0x7610);
+        else w[sl][u >> 1] = f >> 16;
+      }
     }
-    out[0] = __int2bfloat16_rn((int)F);
+    uint4* out = reinterpret_cast<uint4*>(
+        S + ((((long)batch * nrt + r / TR) * nkb + (k >> 6)) * kSlices * TR + r % TR) * 64 + (k & 63));
+#pragma unroll
+    for (int sl = 0; sl < kSlices; ++sl)
+      out[(long)sl * sstride / 8] = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
   }
 }
 
