@@ -509,11 +509,13 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(OzView v, const int* E, _
                                                        int nrt) {
   __shared__ long long t[kST][kST + 1];  // [row][k]
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const long r0 = (long)blockIdx.y * kST, k0 = (long)blockIdx.x * kST;
+  const bool kfast = (v.sK == 1 && v.sR != 1);
+  // blockIdx.x walks the operand's unit-stride direction, so that neighbouring blocks
+  // read neighbouring memory
+  const long r0 = (long)(kfast ? blockIdx.y : blockIdx.x) * kST, k0 = (long)(kfast ? blockIdx.x : blockIdx.y) * kST;
   const int batch = blockIdx.z, bh = batch / v.nblo, bl = batch % v.nblo;
   const long Kt = (long)v.K * v.G;
   const long nkb = Kpad / 64;
-  const bool kfast = (v.sK == 1 && v.sR != 1);
 #pragma unroll 4
   for (int j = 0; j < kST / 4; ++j) {
     const int i = ty + 4 * j;
@@ -614,8 +616,10 @@ void ozaki_slice(attn_ctx* ctx, const OzView& v, long Kpad, int tile_rows, DevBu
             (unsigned)nb);
     oz_exponent_kernel<<<ge, blk, 0, st>>>(v, exps.as<int>());
   }
-  dim3 gs((unsigned)(Kpad / kST), (unsigned)((padded + kST - 1) / kST), (unsigned)nb);
-  ATTN_REQUIRE(gs.y <= 65535, ATTN_EUNSUPPORTED, "too many rows for the split GEMM");
+  const bool kfast = (v.sK == 1 && v.sR != 1);
+  const unsigned nkt = (unsigned)(Kpad / kST), nrb = (unsigned)((padded + kST - 1) / kST);
+  dim3 gs(kfast ? nkt : nrb, kfast ? nrb : nkt, (unsigned)nb);
+  ATTN_REQUIRE(gs.y <= 65535, ATTN_EUNSUPPORTED, "operand too large for the split GEMM");
   oz_slice_kernel<<<gs, dim3(kST, 4), 0, st>>>(v, exps.as<int>(), slices.as<__nv_bfloat16>(), Kpad, tile_rows, nrt);
   ctx->launches += 3;
   ATTN_CHECK_CUDA(cudaGetLastError());
