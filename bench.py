@@ -901,6 +901,8 @@ def main():
     ap.add_argument("--impl", default="attn")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="matvec mode: skip the 16x16 m=128 sweep record")
+    ap.add_argument("--no-solve", action="store_true",
+                    help="matvec mode: skip the mixed-precision local-solve record (profiling runs)")
     ap.add_argument("--sample-s", type=float, default=15.0, help=argparse.SUPPRESS)
     ap.add_argument("--counts", default="", help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -1001,7 +1003,7 @@ def main():
 
     # the accuracy-bearing form of the same solve: BF16 Lanczos then FP64 Rayleigh-Ritz
     # refinement (3 Jacobi-Davidson corrections, FP64 contractions as split BF16 products)
-    solve = mixed_solve_record(attn, ctx, H, x0, torch)
+    solve = None if args.no_solve else mixed_solve_record(attn, ctx, H, x0, torch)
 
     peaks, src = measured_peaks()
     achieved = (k_fl / k_n) / ((k_ms / k_n) / 1000.0) / 1e12 if k_n else None

@@ -131,7 +131,7 @@ __device__ __forceinline__ void block_sum_store(double (&acc)[NV], int n, double
 
 // (A) part[b][i] = block b's share of <basis_i, w>
 template <int NV, int U>
-__global__ void __launch_bounds__(LT) cgs_dot(const double* __restrict__ basis, int n, long V, int D,
+__global__ void __launch_bounds__(LT, 2) cgs_dot(const double* __restrict__ basis, int n, long V, int D,
                                               const double* __restrict__ w, double* part, const double* done) {
   if (done && *done != 0.0) return;
   double acc[NV];
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(LT) cgs_dot(const double* __restrict__ basis, 
 
 // (B) w -= sum_i h_i basis_i, then part[b][i] = block share of <basis_i, w_new>
 template <int NV, int U>
-__global__ void __launch_bounds__(LT) cgs_axpy_dot(double* __restrict__ w, const double* __restrict__ basis,
+__global__ void __launch_bounds__(LT, 2) cgs_axpy_dot(double* __restrict__ w, const double* __restrict__ basis,
                                                    const double* h, int n, long V, int D, double* part,
                                                    const double* done) {
   if (done && *done != 0.0) return;
@@ -166,6 +166,29 @@ __global__ void __launch_bounds__(LT) cgs_axpy_dot(double* __restrict__ w, const
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = 0.0;
   const long stride = (long)gridDim.x * LT;
+  if constexpr (NV == 16 || NV == 20) {
+    // wide bases: each thread parks the basis elements it loads for the update of w in
+    // its own column of shared memory and reads them back for the dot products, so that
+    // only the accumulators stay in registers and two blocks fit on an SM
+    static_assert(U == 1, "the shared-memory form handles one element per thread and pass");
+    __shared__ double sb[NV][LT];
+    for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += stride) {
+      double v = w[e];
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (i < n) {
+          const double bi = basis[bidx(i, e, V, D)];
+          sb[i][threadIdx.x] = bi;
+          v = fma(-c[i], bi, v);
+        }
+      w[e] = v;
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        if (i < n) acc[i] = fma(sb[i][threadIdx.x], v, acc[i]);
+    }
+    block_sum_store<NV>(acc, n, part + (long)blockIdx.x * n);
+    return;
+  }
   for (long e0 = blockIdx.x * (long)LT + threadIdx.x; e0 < V; e0 += stride * U) {
     double b[U][NV], v[U];
 #pragma unroll
@@ -192,7 +215,7 @@ __global__ void __launch_bounds__(LT) cgs_axpy_dot(double* __restrict__ w, const
 
 // (C) w -= sum_i h_i basis_i, then part[b] = block share of ||w_new||^2
 template <int NV, int U>
-__global__ void __launch_bounds__(LT) cgs_axpy_norm(double* __restrict__ w, const double* __restrict__ basis,
+__global__ void __launch_bounds__(LT, 2) cgs_axpy_norm(double* __restrict__ w, const double* __restrict__ basis,
                                                     const double* h, int n, long V, int D, double* part,
                                                     const double* done) {
   if (done && *done != 0.0) return;
@@ -419,6 +442,7 @@ void cgs2_fused(cudaStream_t s, const double* B, int D, double* W, double* S, in
   else if (n <= 8) cgs2_launch<8, 2>(s, B, D, W, S, n, V, nb, part, done);
   else if (n <= 12) cgs2_launch<12, 2>(s, B, D, W, S, n, V, nb, part, done);
   else if (n <= 16) cgs2_launch<16, 1>(s, B, D, W, S, n, V, nb, part, done);
+  else if (n <= 20) cgs2_launch<20, 1>(s, B, D, W, S, n, V, nb, part, done);
   else cgs2_launch<24, 1>(s, B, D, W, S, n, V, nb, part, done);
 }
 
