@@ -347,14 +347,14 @@ SWEEP_L, SWEEP_M, SWEEP_N = 16, 128, 2
 def sweep_record(attn, torch):
     """16x16 TFIM (h = 3.04), m = 128: the first two aTTN sweeps (S_TTN = 1, then
     disentangler updates) of the FP64 path (contractions as split BF16 products) and
-    of the mixed path (BF16 Lanczos + FP64 refinement), from the same tensors."""
+    of the mixed paths (BF16 or TF32 Lanczos + FP64 refinement), from the same tensors."""
     from inputs import raw_tree_tensors
 
     n = SWEEP_L * SWEEP_L
     raw = raw_tree_tensors(tree_shapes(n, SWEEP_M), 0)
     stream = torch.cuda.current_stream().cuda_stream
     out = {}
-    for name in ("f64_split", "mixed_split"):
+    for name in ("f64_split", "mixed_split", "mixed_tf32_split"):
         cfg = arm_config(attn, name)
         ctx = attn.attn_create(cfg, stream)
         model = attn.attn_model_tfim(ctx, SWEEP_L, H_FIELD)
@@ -370,12 +370,14 @@ def sweep_record(attn, torch):
         attn.attn_state_destroy(st)
         attn.attn_model_destroy(model)
         attn.attn_destroy(ctx)
-    out["mixed_minus_f64_per_site"] = [a - b for a, b in zip(out["mixed_split"]["energy_per_site"],
-                                                               out["f64_split"]["energy_per_site"])]
+    for name in ("mixed_split", "mixed_tf32_split"):
+        out[name]["minus_f64_per_site"] = [a - b for a, b in zip(out[name]["energy_per_site"],
+                                                                  out["f64_split"]["energy_per_site"])]
     out["config"] = {"workload": f"tfim{SWEEP_L}x{SWEEP_L}_m{SWEEP_M}_first_{SWEEP_N}_sweeps", "s_ttn": 1,
-                     "mixed": "bf16 Lanczos + <= 8 FP64 Rayleigh-Ritz corrections from 16-step bf16 CG "
-                              "Jacobi-Davidson solves until theta moves by < 1e-10 |theta|; FP64 contractions "
-                              "as split bf16 products (f64_split) in both arms"}
+                     "mixed_split": "bf16 Lanczos + <= 8 FP64 Rayleigh-Ritz corrections from 16-step bf16 CG "
+                                    "Jacobi-Davidson solves until theta moves by < 1e-10 |theta|",
+                     "mixed_tf32_split": "the same with TF32 matvecs",
+                     "contractions": "FP64 contractions as split bf16 products (f64_split) in every arm"}
     return out
 
 

@@ -65,6 +65,9 @@ struct attn_heff {
 
 namespace attn {
 void tc_release(attn_heff* h);
+// Marks the tensor-core copies stale after the H_eff's operators were replaced: the
+// next low-precision application rebuilds them into the same device buffers.
+void tc_invalidate(attn_heff* h);
 bool tc_supported(const attn_heff* h);
 int tc_error(attn_heff* h);
 // Throws ATTN_ETIMEOUT when a bounded wait in a tensor-core kernel gave up (the

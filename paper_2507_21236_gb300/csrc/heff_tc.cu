@@ -493,6 +493,7 @@ struct TcState {
   size_t smem = 0;
   int rsplit = 1;        // products of a slice split over this many CTAs (autotuned)
   bool tuned = false;
+  bool stale = false;    // the H_eff's operators changed since the copies were made
   // three-link products: factors per slot, the slot-2 contraction of one chunk
   // of products ([tchunk][m2][m0][m1]) and the per-product kernel's maps and parameters
   int nt = 0, tchunk = 0;
@@ -524,6 +525,11 @@ bool tc_supported(const attn_heff* h) {
   for (int s = 0; s < 3; ++s)
     if (h->m[s] % 16 != 0 || h->m[s] > 128 || h->m[s] < 16) return false;
   return true;
+}
+
+void tc_invalidate(attn_heff* h) {
+  for (int i = 0; i < 2; ++i)
+    if (h->tc[i]) static_cast<TcState*>(h->tc[i])->stale = true;
 }
 
 void tc_release(attn_heff* h) {
@@ -567,6 +573,21 @@ static TcState* tc_build(attn_heff* h, bool tf) {
   attn_ctx* ctx = h->ctx;
   auto* t = new TcState();
   t->tf = tf;
+  // a stale state of a recycled H_eff hands its device buffers over (they only grow)
+  if (auto* old = static_cast<TcState*>(h->tc[tf ? 1 : 0])) {
+    for (int k = 0; k < 3; ++k) {
+      t->a[k] = std::move(old->a[k]);
+      t->b[k] = std::move(old->b[k]);
+      t->x[k] = std::move(old->x[k]);
+      t->y[k] = std::move(old->y[k]);
+    }
+    t->err = std::move(old->err);
+    t->t0 = std::move(old->t0);
+    t->t1 = std::move(old->t1);
+    t->t2 = std::move(old->t2);
+    t->w = std::move(old->w);
+    delete old;
+  }
   h->tc[tf ? 1 : 0] = t;
   cudaStream_t st = ctx->stream;
   const int* m = h->m;
@@ -698,7 +719,7 @@ void attn_heff::apply_tc(const double* x, double* y, bool tf) {
   ATTN_REQUIRE(tc_supported(this), ATTN_EUNSUPPORTED,
                "the tensor-core path needs every link dimension in {16, 32, ..., 128}");
   TcState* t = static_cast<TcState*>(tc[tf ? 1 : 0]);
-  if (!t) t = tc_build(this, tf);
+  if (!t || t->stale) t = tc_build(this, tf);
   cudaStream_t st = ctx->stream;
   // consumer-side wait limit (a short one is how tests make the kernel give up)
   const int wl = ctx->cfg.wait_limit_log2;

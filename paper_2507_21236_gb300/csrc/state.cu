@@ -349,11 +349,24 @@ void attn_state::renorm_batch(const double* Tc, const int d[3], int t, int x, in
 }
 
 // ------------------------------------------------------------------ H_eff
+void attn_state::recycle(attn_heff* h) {
+  if (!h) return;
+  if (spare_heff) {
+    delete h;
+    return;
+  }
+  delete h->eg;  // a captured graph holds the old operators' launch parameters
+  h->eg = nullptr;
+  attn::tc_invalidate(h);
+  spare_heff = h;
+}
+
 attn_heff* attn_state::build_heff(int n) {
   ATTN_REQUIRE(n == centre, ATTN_EINVAL, "H_eff requested away from the isometry centre");
   Env* E[3];
   for (int s = 0; s < 3; ++s) E[s] = &get_env(n, s);
-  auto* h = new attn_heff();
+  attn_heff* h = spare_heff ? spare_heff : new attn_heff();
+  spare_heff = nullptr;
   h->ctx = ctx;
   for (int s = 0; s < 3; ++s) h->m[s] = dim(n, s);
   h->V = vol(n);
@@ -429,7 +442,7 @@ double attn_state::energy() {
     delete h;
     throw;
   }
-  delete h;
+  recycle(h);
   multi_dot(ctx, tensor(centre), 1, V, y, s, nullptr);
   multi_dot(ctx, tensor(centre), 1, V, tensor(centre), s + 1, nullptr);
   double hv[2];
@@ -501,7 +514,7 @@ double attn_state::local_step(int n) {
     delete h;
     throw;
   }
-  delete h;
+  recycle(h);
   return result;
 }
 

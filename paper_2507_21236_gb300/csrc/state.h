@@ -78,6 +78,16 @@ struct attn_state {
   attn::LanczosWork lw, lw2;
   attn::RefineWork rfw;
   attn::DevBuf colbuf, rbuf, tmpT, idxbuf, opsA, opsB, rw1, rw2;
+  // The H_eff of the last local step, kept with its device buffers so that the next
+  // build reuses them (its operator stacks and their tensor-core copies take hundreds
+  // of MB at m = 128; allocating and freeing them every step cost milliseconds and a
+  // device synchronisation each).
+  attn_heff* spare_heff = nullptr;
+  attn_state() = default;
+  attn_state(const attn_state&) = delete;
+  attn_state& operator=(const attn_state&) = delete;
+  ~attn_state() { delete spare_heff; }
+  void recycle(attn_heff* h);
 
   int dim(int n, int s) const { return tree.shape[3 * n + s]; }
   long vol(int n) const { return (long)dim(n, 0) * dim(n, 1) * dim(n, 2); }
