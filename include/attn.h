@@ -103,7 +103,11 @@ typedef struct {
                                three); the same linear map with fewer products (0) */
   int de_method;            /* disentangler optimisation: 0 = MERA-like self-consistent update (Sec. 4.1.1),
                                1 = Riemannian conjugate gradients of the true E_k on O(4) (Sec. 4.1.2) (0) */
-  int reserved[1];
+  int tc_schedule;          /* grid of the tensor-core H_eff kernel: 0 = chosen by timing at the first
+                               application (the split grid or the persistent form, whichever is faster), 1 =
+                               split grid (one CTA per slice pair and product range), 2 = persistent (one CTA per
+                               SM over a cost-balanced cut of the node's products). Results agree to FP32
+                               rounding either way (0) */
 } attn_config;
 
 ATTN_API attn_status attn_config_default(attn_config* cfg);

@@ -222,6 +222,7 @@ ATTN_API attn_status attn_set_config(attn_ctx* ctx, const attn_config* cfg) {
                ATTN_EUNSUPPORTED, "matvec_dtype must be ATTN_F64, ATTN_TF32 or ATTN_BF16");
   ATTN_REQUIRE(cfg->wait_limit_log2 >= 0 && cfg->wait_limit_log2 <= 62, ATTN_EINVAL, "wait_limit_log2 must be 0..62");
   ATTN_REQUIRE(cfg->de_method == 0 || cfg->de_method == 1, ATTN_EINVAL, "de_method must be 0 or 1");
+  ATTN_REQUIRE(cfg->tc_schedule >= 0 && cfg->tc_schedule <= 2, ATTN_EINVAL, "tc_schedule must be 0, 1 or 2");
   ctx->cfg = *cfg;
   ATTN_CATCH
 }
@@ -655,10 +656,10 @@ static void eigsolve_dev(attn_heff* h, double* T_dev, double* theta, int* iters)
     EigGraph* g = h->eg;
     // a graph holds the addresses of the context's scratch buffers at capture time:
     // any reallocation since (scratch_epoch) or a change of the FP64 contraction path
-    // (f64_split) makes it stale
+    // (f64_split) or of the tensor-core grid (tc_schedule) makes it stale
     if (!g || g->x != T_dev || g->depth != cfg.lanczos_depth || g->tol != cfg.lanczos_tol || g->dtype != dt ||
         g->refine != rsteps || g->rtol != cfg.refine_tol || g->prof != ctx->prof_on ||
-        g->f64_split != cfg.f64_split || g->epoch != ctx->scratch_epoch) {
+        g->f64_split != cfg.f64_split || g->tc_schedule != cfg.tc_schedule || g->epoch != ctx->scratch_epoch) {
       delete g;
       g = h->eg = new EigGraph();
       g->x = T_dev;
@@ -669,6 +670,7 @@ static void eigsolve_dev(attn_heff* h, double* T_dev, double* theta, int* iters)
       g->rtol = cfg.refine_tol;
       g->prof = ctx->prof_on;
       g->f64_split = cfg.f64_split;
+      g->tc_schedule = cfg.tc_schedule;
       // warm-up on a scratch copy: every buffer the solve needs is allocated before capture
       ctx->ws[3].reserve(sizeof(double) * h->V);
       copy_f64(ctx, ctx->ws[3].as<double>(), T_dev, h->V);

@@ -92,6 +92,17 @@ struct TcParams {
   int nkinds;
   int* err;           // device error word (0 = ok)
   long long wait;     // wait limit (cycles) of the MMA-issue, conversion and epilogue threads
+  // Persistent form (segs != null): CTA b walks segments seg_start[b] .. seg_start[b + 1] - 1
+  // of a cost-balanced cut of the node's (kind, slice pair, product) list; otherwise each
+  // CTA owns one (kind, slice pair, product range) given by its index and the kinds' splits.
+  const int4* segs;   // {kind, slice pair, first product, products | 1 << 30 when added atomically}
+  const int* seg_start;
+};
+
+// One CTA's share of the work: products r0 .. r0 + n - 1 of slice pair `pair` of a kind.
+struct Seg {
+  int kind, pair, r0, n;
+  bool atomic;  // the pair's output is shared with other CTAs (or adds onto an earlier result)
 };
 
 struct TcMaps {
@@ -133,32 +144,53 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     D1FULL = 1 + 2 * NS,  // [slice]: stage 1 done
     ZFULL = 3 + 2 * NS,   // [slice][half]: that half of Z^T packed in TMEM
     S2DONE = 7 + 2 * NS,  // [slice]: stage 2 done, D1 free for the next product
-    D2FULL = 9 + 2 * NS,
-    S1END = 10 + 2 * NS,  // every stage-1 MMA complete (TMEM may be freed)
-    NBAR = 11 + 2 * NS
+    D2FULL = 9 + 2 * NS,  // a segment's stage 2 complete
+    S1END = 10 + 2 * NS,  // [issuer]: every MMA of that issuer complete (TMEM may be freed)
+    XEMPTY = 12 + 2 * NS, // a segment's stage-1 MMAs complete: its X may be replaced
+    D2EMPTY = 13 + 2 * NS,  // the epilogue has read a segment's D2
+    NBAR = 14 + 2 * NS
   };
   uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + (sBar - base));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   auto bar = [&](int i) { return sBar + 8u * (uint32_t)i; };
 
-  // which kind / slice pair / product range does this CTA own?
+  // the CTA's segments: one per CTA (split grid), or a cost-balanced run of them (persistent)
+  const int nseg = prm.segs ? prm.seg_start[blockIdx.x + 1] - prm.seg_start[blockIdx.x] : 1;
+  auto seg_at = [&](int j) {
+    Seg g;
+    if (prm.segs) {
+      const int4 v = prm.segs[prm.seg_start[blockIdx.x] + j];
+      g.kind = v.x;
+      g.pair = v.y;
+      g.r0 = v.z;
+      g.n = v.w & 0x3FFFFFFF;
+      g.atomic = (v.w >> 30) & 1;
+      return g;
+    }
+    g.kind = 0;
+    if (prm.nkinds > 1 && (int)blockIdx.x >= prm.kind[1].cta_begin) g.kind = 1;
+    if (prm.nkinds > 2 && (int)blockIdx.x >= prm.kind[2].cta_begin) g.kind = 2;
+    const KindParams& k = g.kind == 0 ? prm.kind[0] : (g.kind == 1 ? prm.kind[1] : prm.kind[2]);
+    const int local = blockIdx.x - k.cta_begin;
+    const int part = local % k.rsplit;
+    g.pair = local / k.rsplit;
+    g.r0 = (int)((long)k.R * part / k.rsplit);
+    g.n = (int)((long)k.R * (part + 1) / k.rsplit) - g.r0;
+    g.atomic = k.rsplit > 1 || k.accumulate;
+    return g;
+  };
   // (static indices only: a runtime index into the parameter struct would copy it to local memory)
-  int kind = 0;
-  KindParams kp = prm.kind[0];
-  if (prm.nkinds > 1 && (int)blockIdx.x >= prm.kind[1].cta_begin) { kind = 1; kp = prm.kind[1]; }
-  if (prm.nkinds > 2 && (int)blockIdx.x >= prm.kind[2].cta_begin) { kind = 2; kp = prm.kind[2]; }
-  const int local = blockIdx.x - kp.cta_begin;
-  const int pair = local / kp.rsplit, part = local % kp.rsplit;
-  const int s0 = 2 * pair;
-  const int nsl = (s0 + 1 < kp.S) ? 2 : 1;
-  const int r_begin = (int)((long)kp.R * part / kp.rsplit);
-  const int R = (int)((long)kp.R * (part + 1) / kp.rsplit) - r_begin;
-  const int P = kp.P, Q = kp.Q;
+  auto kind_of = [&](int k) -> KindParams {
+    if (k == 1) return prm.kind[1];
+    if (k == 2) return prm.kind[2];
+    return prm.kind[0];
+  };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     mbar_init(bar(XFULL), 1);
+    mbar_init(bar(XEMPTY), 1);
     for (int i = 0; i < NS; ++i) {
       mbar_init(bar(FULL + i), 1);
       mbar_init(bar(EMPTY + i), 1);
@@ -169,7 +201,9 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     }
     for (int i = 0; i < 4; ++i) mbar_init(bar(ZFULL + i), kHalfWarps);
     mbar_init(bar(D2FULL), 1);
+    mbar_init(bar(D2EMPTY), 16);
     mbar_init(bar(S1END), 1);
+    mbar_init(bar(S1END + 1), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -186,49 +220,60 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
   // TMEM: D1 of slice u in columns 128u .. 128u+P-1 (Z^T packed in place), D2 of slice u at 256 + 128u
   auto tD1 = [&](int u) { return tmem + 128u * (uint32_t)u; };
   auto tD2 = [&](int u) { return tmem + 256u + 128u * (uint32_t)u; };
-  const int nkbQ = (Q + KB - 1) / KB, nkbP = (P + KB - 1) / KB;
-  const CUtensorMap* mX = &maps.x[kind];
-  const CUtensorMap* mA = &maps.a[kind];
-  const CUtensorMap* mB = &maps.b[kind];
 
   if (warp == 0 && lane == 0) {
-    // ---- producer: X of both slices once (or per product when kPP), then the
-    // operator K blocks in consumption order
-    if (!kPP) {
-      mbar_expect_tx(bar(XFULL), (uint32_t)(nsl * nkbQ * P * 128));
-      for (int u = 0; u < nsl; ++u)
-        for (int kb = 0; kb < nkbQ; ++kb)
-          tma_load_3d(sX + kb * kTileBytes + u * (kTileBytes / 2), mX, KB * kb, 0, s0 + u, bar(XFULL));
-    }
-    int issued = 0;
+    // ---- producer: per segment X of both slices (or per product when kPP), then the
+    // operator K blocks in consumption order; X of a segment is loaded once the stage-1
+    // MMAs of the previous one have read theirs
+    int issued = 0, xissued = 0;
     int st = 0;       // ring stage of the next load
     uint32_t ph = 0;  // parity of that stage's current fill
     bool ok = true;
-    const int nparts = kPP ? 2 + nsl : 2;  // B_r, [X_{r,s0}, X_{r,s0+1}], A_r
-    for (int r = 0; ok && r < R; ++r) {
-      for (int part = 0; ok && part < nparts; ++part) {
-        const bool isB = part == 0, isA = part == nparts - 1;
-        const CUtensorMap* mp = isB ? mB : (isA ? mA : mX);
-        const int nkb = isA ? nkbP : nkbQ;
-        const int z = isB || isA ? r_begin + r : (r_begin + r) * kp.S + s0 + (part - 1);
-        const uint32_t bytes = isB || isA ? (uint32_t)kKBlockBytes : (uint32_t)(P * 128);
-        for (int kb = 0; kb < nkb; ++kb) {
-          // the stage's previous contents (fill ph - 1) must have been consumed
-          if (issued >= NS && !mbar_wait(bar(EMPTY + st), ph ^ 1u, prm.err, 11, abort_flag)) {
-            ok = false;
-            break;
+    for (int j = 0; ok && j < nseg; ++j) {
+      const Seg g = seg_at(j);
+      const KindParams kp = kind_of(g.kind);
+      const int P = kp.P, Q = kp.Q, s0 = 2 * g.pair, nsl = (s0 + 1 < kp.S) ? 2 : 1;
+      const int nkbQ = (Q + KB - 1) / KB, nkbP = (P + KB - 1) / KB;
+      const CUtensorMap* mX = &maps.x[g.kind];
+      const CUtensorMap* mA = &maps.a[g.kind];
+      const CUtensorMap* mB = &maps.b[g.kind];
+      if (!kPP) {
+        if (j > 0 && !mbar_wait(bar(XEMPTY), (j - 1) & 1, prm.err, 12, abort_flag)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(bar(XFULL), (uint32_t)(nsl * nkbQ * P * 128));
+        for (int u = 0; u < nsl; ++u)
+          for (int kb = 0; kb < nkbQ; ++kb)
+            tma_load_3d(sX + kb * kTileBytes + u * (kTileBytes / 2), mX, KB * kb, 0, s0 + u, bar(XFULL));
+        ++xissued;
+      }
+      const int nparts = kPP ? 2 + nsl : 2;  // B_r, [X_{r,s0}, X_{r,s0+1}], A_r
+      for (int r = 0; ok && r < g.n; ++r) {
+        for (int part = 0; ok && part < nparts; ++part) {
+          const bool isB = part == 0, isA = part == nparts - 1;
+          const CUtensorMap* mp = isB ? mB : (isA ? mA : mX);
+          const int nkb = isA ? nkbP : nkbQ;
+          const int z = isB || isA ? g.r0 + r : (g.r0 + r) * kp.S + s0 + (part - 1);
+          const uint32_t bytes = isB || isA ? (uint32_t)kKBlockBytes : (uint32_t)(P * 128);
+          for (int kb = 0; kb < nkb; ++kb) {
+            // the stage's previous contents (fill ph - 1) must have been consumed
+            if (issued >= NS && !mbar_wait(bar(EMPTY + st), ph ^ 1u, prm.err, 11, abort_flag)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(bar(FULL + st), bytes);
+            tma_load_3d(sRing + st * kKBlockBytes, mp, KB * kb, 0, z, bar(FULL + st));
+            ++issued;
+            if (++st == NS) { st = 0; ph ^= 1u; }
           }
-          mbar_expect_tx(bar(FULL + st), bytes);
-          tma_load_3d(sRing + st * kKBlockBytes, mp, KB * kb, 0, z, bar(FULL + st));
-          ++issued;
-          if (++st == NS) { st = 0; ph ^= 1u; }
         }
       }
     }
     // drain: wait (bounded) until every issued load has landed
-    if (!kPP) {
+    if (xissued > 0) {
       long long t0 = clock64();
-      while (!mbar_try_wait(bar(XFULL), 0) && clock64() - t0 < kWaitCycles) {}
+      while (!mbar_try_wait(bar(XFULL), (xissued - 1) & 1) && clock64() - t0 < kWaitCycles) {}
     }
     for (int q = (issued > NS ? issued - NS : 0); q < issued; ++q) {
       long long t0 = clock64();
@@ -239,8 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     // single thread cannot issue N = 128 MMAs (64 cycles each) back to back once
     // waits and commits are interleaved. Warp 1 issues stage 1, warp 2 stage 2;
     // the pipe sees S1(r,0), S1(r,1), S2(r,0), S2(r,1), S1(r+1,0), ...
-    const uint32_t id = idesc_of<kTF>(128, P);  // both stages: M = 128 TMEM lanes, N = P
-    const int nk16Q = Q / KS, nk16P = P / KS;   // MMA K steps
+    // Barrier phases count products per slice across segments (cnt[u]).
     const uint64_t dRing0 = sw128_desc(sRing);  // ring stage st: + st * (kKBlockBytes >> 4)
     const uint32_t barFull = bar(FULL), barEmpty = bar(EMPTY);
     int st = 0;        // ring stage of the product's first K block
@@ -249,86 +293,128 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
       for (int i = 0; i < n; ++i)
         if (++st == NS) { st = 0; ph ^= 1u; }
     };
-    const int nkbX = kPP ? nsl * nkbQ : 0;  // ring K blocks of X per product
+    int cnt[2] = {0, 0};
+    bool ok = true;
     if (warp == 1) {
       const uint64_t dX0 = sw128_desc(sX);  // X block kb of slice u: + (32 KB kb + 16 KB u) >> 4
-      bool ok = kPP ? true : mbar_wait(bar(XFULL), 0, prm.err, 31, abort_flag, prm.wait);
-      for (int r = 0; ok && r < R; ++r) {
-        // stage 1 per slice: D1_u = B_r X_u^T (the B_r blocks serve both slices)
-        for (int u = 0; ok && u < nsl; ++u) {
-          // D1_u holds Z_u of product r-1 until its stage 2 has completed
-          if (r > 0 && !mbar_wait(bar(S2DONE + u), (r - 1) & 1, prm.err, 35, abort_flag, prm.wait)) { ok = false; break; }
-          fence_after();
-          int s1 = st;
-          uint32_t p1 = ph;
-          int sx = st + nkbQ * (1 + u);  // ring stage of this slice's first X block (kPP)
-          uint32_t px = ph;
-          while (sx >= NS) { sx -= NS; px ^= 1u; }
-          for (int kb = 0; kb < nkbQ; ++kb) {
-            if (u == 0 && !mbar_wait(barFull + 8 * s1, p1, prm.err, 32, abort_flag, prm.wait)) { ok = false; break; }
-            if (kPP && !mbar_wait(barFull + 8 * sx, px, prm.err, 36, abort_flag, prm.wait)) { ok = false; break; }
-            const uint64_t dB = dRing0 + (uint64_t)(s1 * (kKBlockBytes >> 4));
-            const uint64_t dX = kPP ? dRing0 + (uint64_t)(sx * (kKBlockBytes >> 4))
-                                    : dX0 + (uint64_t)((kb * kTileBytes + u * (kTileBytes / 2)) >> 4);
-            const int n4 = nk16Q - 4 * kb;
-            if (n4 >= 4) {
-              mma4_ss_t<kTF>(tD1(u), dB, dX, id, kb > 0 ? 1u : 0u);
-            } else {
-              for (int k4 = 0; k4 < n4; ++k4)
-                mma_ss<kTF>(tD1(u), dB + 2 * k4, dX + 2 * k4, id, (kb > 0 || k4 > 0) ? 1u : 0u);
+      for (int j = 0; ok && j < nseg; ++j) {
+        const Seg g = seg_at(j);
+        const KindParams kp = kind_of(g.kind);
+        const int P = kp.P, Q = kp.Q, nsl = (2 * g.pair + 1 < kp.S) ? 2 : 1;
+        const int nkbQ = (Q + KB - 1) / KB, nkbP = (P + KB - 1) / KB;
+        const int nkbX = kPP ? nsl * nkbQ : 0;  // ring K blocks of X per product
+        const uint32_t id = idesc_of<kTF>(128, P);  // both stages: M = 128 TMEM lanes, N = P
+        const int nk16Q = Q / KS;
+        if (!kPP && !mbar_wait(bar(XFULL), j & 1, prm.err, 31, abort_flag, prm.wait)) { ok = false; break; }
+        for (int r = 0; ok && r < g.n; ++r) {
+          // stage 1 per slice: D1_u = B_r X_u^T (the B_r blocks serve both slices)
+          for (int u = 0; ok && u < nsl; ++u) {
+            // D1_u holds Z_u of the previous product until its stage 2 has completed
+            if (cnt[u] > 0 && !mbar_wait(bar(S2DONE + u), (cnt[u] - 1) & 1, prm.err, 35, abort_flag, prm.wait)) {
+              ok = false;
+              break;
             }
-            if (u == nsl - 1) mma_commit(barEmpty + 8 * s1);
-            if (kPP) mma_commit(barEmpty + 8 * sx);
-            if (++s1 == NS) { s1 = 0; p1 ^= 1u; }
-            if (++sx == NS) { sx = 0; px ^= 1u; }
+            fence_after();
+            int s1 = st;
+            uint32_t p1 = ph;
+            int sx = st + nkbQ * (1 + u);  // ring stage of this slice's first X block (kPP)
+            uint32_t px = ph;
+            while (sx >= NS) { sx -= NS; px ^= 1u; }
+            for (int kb = 0; kb < nkbQ; ++kb) {
+              if (u == 0 && !mbar_wait(barFull + 8 * s1, p1, prm.err, 32, abort_flag, prm.wait)) { ok = false; break; }
+              if (kPP && !mbar_wait(barFull + 8 * sx, px, prm.err, 36, abort_flag, prm.wait)) { ok = false; break; }
+              const uint64_t dB = dRing0 + (uint64_t)(s1 * (kKBlockBytes >> 4));
+              const uint64_t dX = kPP ? dRing0 + (uint64_t)(sx * (kKBlockBytes >> 4))
+                                      : dX0 + (uint64_t)((kb * kTileBytes + u * (kTileBytes / 2)) >> 4);
+              const int n4 = nk16Q - 4 * kb;
+              if (n4 >= 4) {
+                mma4_ss_t<kTF>(tD1(u), dB, dX, id, kb > 0 ? 1u : 0u);
+              } else {
+                for (int k4 = 0; k4 < n4; ++k4)
+                  mma_ss<kTF>(tD1(u), dB + 2 * k4, dX + 2 * k4, id, (kb > 0 || k4 > 0) ? 1u : 0u);
+              }
+              if (u == nsl - 1) mma_commit(barEmpty + 8 * s1);
+              if (kPP) mma_commit(barEmpty + 8 * sx);
+              if (++s1 == NS) { s1 = 0; p1 ^= 1u; }
+              if (++sx == NS) { sx = 0; px ^= 1u; }
+            }
+            if (!ok) break;
+            mma_commit(bar(D1FULL + u));
+            ++cnt[u];
           }
-          if (!ok) break;
-          mma_commit(bar(D1FULL + u));
+          advance(nkbQ + nkbX + nkbP);
         }
-        advance(nkbQ + nkbX + nkbP);
+        // once these MMAs complete, the segment's X is no longer read
+        if (ok && !kPP) mma_commit(bar(XEMPTY));
       }
       mma_commit(bar(S1END));
       long long t0 = clock64();
       while (!mbar_try_wait(bar(S1END), 0) && clock64() - t0 < kWaitCycles) {}
     } else {
-      bool ok = true;
-      for (int r = 0; ok && r < R; ++r) {
-        advance(nkbQ + nkbX);
-        // stage 2 per slice: D2_u += Z_u^T A_r^T, Z_u read from TMEM half by half
-        for (int u = 0; ok && u < nsl; ++u) {
-          int s2 = st;
-          uint32_t p2 = ph;
-          for (int kb = 0; kb < nkbP; ++kb) {
-            // BF16: each 64-column half of Z^T once the conversion warps packed it;
-            // TF32: the whole stage-1 result once its MMAs are complete
-            if (kTF ? (kb == 0 && !mbar_wait(bar(D1FULL + u), r & 1, prm.err, 34, abort_flag, prm.wait))
-                    : !mbar_wait(bar(ZFULL + 2 * u + kb), r & 1, prm.err, 34, abort_flag, prm.wait)) {
-              ok = false;
-              break;
+      int done = 0;  // segments whose stage-2 MMAs were committed to D2FULL
+      uint32_t zpar = 0;  // bit 2 u + h: parity of the products consumed from [slice u][half h] (ZFULL)
+      for (int j = 0; ok && j < nseg; ++j) {
+        const Seg g = seg_at(j);
+        const KindParams kp = kind_of(g.kind);
+        const int P = kp.P, Q = kp.Q, nsl = (2 * g.pair + 1 < kp.S) ? 2 : 1;
+        const int nkbQ = (Q + KB - 1) / KB, nkbP = (P + KB - 1) / KB;
+        const int nkbX = kPP ? nsl * nkbQ : 0;
+        const uint32_t id = idesc_of<kTF>(128, P);
+        const int nk16P = P / KS;
+        for (int r = 0; ok && r < g.n; ++r) {
+          advance(nkbQ + nkbX);
+          // stage 2 per slice: D2_u += Z_u^T A_r^T, Z_u read from TMEM half by half
+          for (int u = 0; ok && u < nsl; ++u) {
+            int s2 = st;
+            uint32_t p2 = ph;
+            for (int kb = 0; kb < nkbP; ++kb) {
+              // BF16: each 64-column half of Z^T once the conversion warps packed it;
+              // TF32: the whole stage-1 result once its MMAs are complete
+              if (kTF ? (kb == 0 && !mbar_wait(bar(D1FULL + u), cnt[u] & 1, prm.err, 34, abort_flag, prm.wait))
+                      : !mbar_wait(bar(ZFULL + 2 * u + kb), (zpar >> (2 * u + kb)) & 1u, prm.err, 34, abort_flag,
+                                   prm.wait)) {
+                ok = false;
+                break;
+              }
+              if (!kTF) zpar ^= 1u << (2 * u + kb);
+              // the segment's first MMA restarts D2: the epilogue must have read the last one's
+              if (j > 0 && r == 0 && u == 0 && kb == 0 &&
+                  !mbar_wait(bar(D2EMPTY), (j - 1) & 1, prm.err, 37, abort_flag, prm.wait)) {
+                ok = false;
+                break;
+              }
+              if (u == 0 && !mbar_wait(barFull + 8 * s2, p2, prm.err, 33, abort_flag, prm.wait)) { ok = false; break; }
+              fence_after();  // Z was written by tcgen05.st in other threads (BF16) or by MMAs
+              const uint64_t dA = dRing0 + (uint64_t)(s2 * (kKBlockBytes >> 4));
+              const uint32_t aZ = tD1(u) + (kTF ? 32u : 64u) * (uint32_t)kb;
+              const int n4 = nk16P - 4 * kb;
+              if (n4 >= 4) {
+                mma4_ts_t<kTF>(tD2(u), aZ, dA, id, (r > 0 || kb > 0) ? 1u : 0u);
+              } else {
+                for (int k4 = 0; k4 < n4; ++k4)
+                  mma_ts<kTF>(tD2(u), aZ + 8 * k4, dA + 2 * k4, id, (r > 0 || kb > 0 || k4 > 0) ? 1u : 0u);
+              }
+              if (u == nsl - 1) mma_commit(barEmpty + 8 * s2);
+              if (++s2 == NS) { s2 = 0; p2 ^= 1u; }
             }
-            if (u == 0 && !mbar_wait(barFull + 8 * s2, p2, prm.err, 33, abort_flag, prm.wait)) { ok = false; break; }
-            fence_after();  // Z was written by tcgen05.st in other threads (BF16) or by MMAs
-            const uint64_t dA = dRing0 + (uint64_t)(s2 * (kKBlockBytes >> 4));
-            const uint32_t aZ = tD1(u) + (kTF ? 32u : 64u) * (uint32_t)kb;
-            const int n4 = nk16P - 4 * kb;
-            if (n4 >= 4) {
-              mma4_ts_t<kTF>(tD2(u), aZ, dA, id, (r > 0 || kb > 0) ? 1u : 0u);
-            } else {
-              for (int k4 = 0; k4 < n4; ++k4)
-                mma_ts<kTF>(tD2(u), aZ + 8 * k4, dA + 2 * k4, id, (r > 0 || kb > 0 || k4 > 0) ? 1u : 0u);
-            }
-            if (u == nsl - 1) mma_commit(barEmpty + 8 * s2);
-            if (++s2 == NS) { s2 = 0; p2 ^= 1u; }
+            if (!ok) break;
+            mma_commit(bar(S2DONE + u));
+            ++cnt[u];
           }
-          if (!ok) break;
-          mma_commit(bar(S2DONE + u));
+          advance(nkbP);
         }
-        advance(nkbP);
+        if (!ok) break;
+        mma_commit(bar(D2FULL));
+        ++done;
       }
-      mma_commit(bar(D2FULL));
       // every MMA this thread issued must finish before TMEM can be freed
+      if (done > 0) {
+        long long t0 = clock64();
+        while (!mbar_try_wait(bar(D2FULL), (done - 1) & 1) && clock64() - t0 < kWaitCycles) {}
+      }
+      mma_commit(bar(S1END + 1));
       long long t0 = clock64();
-      while (!mbar_try_wait(bar(D2FULL), 0) && clock64() - t0 < kWaitCycles) {}
+      while (!mbar_try_wait(bar(S1END + 1), 0) && clock64() - t0 < kWaitCycles) {}
     }
   } else if (warp >= 4) {
     // ---- conversion D1 -> packed BF16 Z^T and the epilogue. Slice u has warps
@@ -337,48 +423,69 @@ __global__ void __launch_bounds__(kThreads, 1) sandwich_tc_kernel(const __grid_c
     const int cw = warp - 4;
     const int u = cw >> 3, hh = (cw >> 2) & 1;
     const int q4 = warp & 3;
-    const int j = q4 * 32 + lane;  // TMEM lane == row j of D1 and of D2 = Y^T
+    const int jl = q4 * 32 + lane;  // TMEM lane == row jl of D1 and of D2 = Y^T
     const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
     const int c0 = 64 * hh;
     const uint32_t tz = tD1(u) + lane_off + (uint32_t)c0;
-    bool ok = u < nsl && c0 < P;
-    for (int r = 0; !kTF && ok && r < R; ++r) {
-      // warp-uniform: the TMEM accesses below are .sync.aligned
-      if (!__all_sync(0xffffffffu, mbar_wait(bar(D1FULL + u), r & 1, prm.err, 41, abort_flag, prm.wait))) { ok = false; break; }
-      fence_after();
-      uint32_t w[32];  // packed BF16 pairs of this thread's 64 columns
+    int cnt = 0;  // stage-1 results of this warp's slice so far (D1FULL phases), converted or not
+    bool ok = true;
+    for (int j = 0; ok && j < nseg; ++j) {
+      const Seg g = seg_at(j);
+      const KindParams kp = kind_of(g.kind);
+      const int P = kp.P, Q = kp.Q, s0 = 2 * g.pair, nsl = (s0 + 1 < kp.S) ? 2 : 1;
+      const bool mine = u < nsl && c0 < P;  // this warp's columns exist in this segment
+      for (int r = 0; !kTF && mine && r < g.n; ++r) {
+        // warp-uniform: the TMEM accesses below are .sync.aligned
+        if (!__all_sync(0xffffffffu, mbar_wait(bar(D1FULL + u), cnt & 1, prm.err, 41, abort_flag, prm.wait))) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        uint32_t w[32];  // packed BF16 pairs of this thread's 64 columns
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        float v[32];
-        tmem_ld32(tz + 32 * t, v);
+        for (int t = 0; t < 2; ++t) {
+          float v[32];
+          tmem_ld32(tz + 32 * t, v);
 #pragma unroll
-        for (int h = 0; h < 16; ++h) w[16 * t + h] = pack_bf16(v[2 * h], v[2 * h + 1]);
+          for (int h = 0; h < 16; ++h) w[16 * t + h] = pack_bf16(v[2 * h], v[2 * h + 1]);
+        }
+        tmem_st32(tz, w);
+        fence_before();
+        // one arrival per warp: 256 arrivals on one barrier would serialise on its word
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(ZFULL + 2 * u + hh));
+        ++cnt;
       }
-      tmem_st32(tz, w);
-      fence_before();
-      // one arrival per warp: 256 arrivals on one barrier would serialise on its word
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar(ZFULL + 2 * u + hh));
-    }
-    if (ok && R > 0 && __all_sync(0xffffffffu, mbar_wait(bar(D2FULL), 0, prm.err, 43, abort_flag, prm.wait))) {
+      if (!ok) break;
+      // a slice whose columns lie outside this warp's half still advanced D1FULL
+      if (!kTF && !mine && u < nsl) cnt += g.n;
+      // the segment's result; every warp takes part in the phases, whether it has columns or not
+      if (!__all_sync(0xffffffffu, mbar_wait(bar(D2FULL), j & 1, prm.err, 43, abort_flag, prm.wait))) {
+        ok = false;
+        break;
+      }
       fence_after();
-      float* yp = kp.Y + ((long)(s0 + u) * P + c0) * Q + j;  // walks down column j of Y_s
-      // partial sums of a split product list meet here, and per-product results add onto the pair result
-      const bool add = kp.rsplit > 1 || kp.accumulate;
-      for (int cc = c0; cc < c0 + 64 && cc < P; cc += 32) {
-        float v[32];
-        tmem_ld32(tD2(u) + lane_off + cc, v);  // v[c] = Y_s[cc + c][j]
-        if (j < Q) {
+      if (mine && g.n > 0) {
+        float* yp = kp.Y + ((long)(s0 + u) * P + c0) * Q + jl;  // walks down column jl of Y_s
+        // partial sums of a shared product list meet here, and per-product results add onto the pair result
+        for (int cc = c0; cc < c0 + 64 && cc < P; cc += 32) {
+          float v[32];
+          tmem_ld32(tD2(u) + lane_off + cc, v);  // v[c] = Y_s[cc + c][jl]
+          if (jl < Q) {
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            if (cc + c < P) {
-              if (add) atomicAdd(yp, v[c]);
-              else *yp = v[c];
+            for (int c = 0; c < 32; ++c) {
+              if (cc + c < P) {
+                if (g.atomic) atomicAdd(yp, v[c]);
+                else *yp = v[c];
+              }
+              yp += Q;
             }
-            yp += Q;
           }
         }
       }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(D2EMPTY));
     }
   }
   fence_before();
@@ -494,6 +601,12 @@ struct TcState {
   int rsplit = 1;        // products of a slice split over this many CTAs (autotuned)
   bool tuned = false;
   bool stale = false;    // the H_eff's operators changed since the copies were made
+  // persistent form: one CTA per SM over a cost-balanced cut of the work list
+  bool persistent = false, seg_atomic = false;
+  int pgrid = 0;
+  std::vector<int4> hsegs;
+  std::vector<int> hstart;
+  DevBuf segs, seg_start;
   // three-link products: factors per slot, the slot-2 contraction of one chunk
   // of products ([tchunk][m2][m0][m1]) and the per-product kernel's maps and parameters
   int nt = 0, tchunk = 0;
@@ -503,7 +616,18 @@ struct TcState {
   size_t es() const { return tf ? 4 : 2; }
   // Split every kind's product list f ways (at least 8 products per CTA) and lay out
   // the grid: one CTA per slice pair and product range.
+  // f >= 1: split grid (products of a slice pair over f CTAs); f = 0: persistent form
   void set_split(int f) {
+    persistent = f == 0;
+    rsplit = f;
+    if (persistent) {
+      prm.segs = segs.as<int4>();
+      prm.seg_start = seg_start.as<int>();
+      grid = pgrid;
+      return;
+    }
+    prm.segs = nullptr;
+    prm.seg_start = nullptr;
     int cta = 0;
     for (int k = 0; k < prm.nkinds; ++k) {
       KindParams& kp = prm.kind[k];
@@ -515,9 +639,53 @@ struct TcState {
     rsplit = f;
   }
   bool split_any() const {
+    if (persistent) return seg_atomic;
     for (int k = 0; k < prm.nkinds; ++k)
       if (prm.kind[k].rsplit > 1) return true;
     return false;
+  }
+  // Cut the work list (kind, slice pair, product), each product weighted by its MMA work
+  // P + Q, into G runs of equal cost, one per CTA; a slice pair whose products land in
+  // more than one run is summed atomically.
+  void build_segments(int G, cudaStream_t st) {
+    double total = 0.0;
+    for (int k = 0; k < prm.nkinds; ++k)
+      total += (double)((prm.kind[k].S + 1) / 2) * prm.kind[k].R * (prm.kind[k].P + prm.kind[k].Q);
+    hsegs.clear();
+    hstart.assign(G + 1, 0);
+    const double per = total / G;
+    double pos = 0.0;
+    int cur = -1;  // CTA of the last segment
+    seg_atomic = false;
+    for (int k = 0; k < prm.nkinds; ++k) {
+      const KindParams& kp = prm.kind[k];
+      const double w = kp.P + kp.Q;
+      for (int pair = 0; pair < (kp.S + 1) / 2; ++pair) {
+        const size_t first = hsegs.size();
+        for (int r = 0; r < kp.R; ++r, pos += w) {
+          const int c = std::min(G - 1, (int)(pos / per));
+          if (hsegs.size() > first && c == cur && hsegs.back().x == k && hsegs.back().y == pair) {
+            ++hsegs.back().w;
+          } else {
+            for (int cc = cur + 1; cc <= c; ++cc) hstart[cc] = (int)hsegs.size();
+            hsegs.push_back(make_int4(k, pair, r, 1));
+            cur = c;
+          }
+        }
+        const bool shared = hsegs.size() - first > 1;
+        for (size_t i = first; i < hsegs.size(); ++i)
+          if (shared || kp.accumulate) {
+            hsegs[i].w |= 1 << 30;
+            seg_atomic = true;
+          }
+      }
+    }
+    for (int cc = cur + 1; cc <= G; ++cc) hstart[cc] = (int)hsegs.size();
+    segs.reserve(sizeof(int4) * std::max<size_t>(hsegs.size(), 1));
+    seg_start.reserve(sizeof(int) * (size_t)(G + 1));
+    ATTN_CHECK_CUDA(cudaMemcpyAsync(segs.p, hsegs.data(), sizeof(int4) * hsegs.size(), cudaMemcpyHostToDevice, st));
+    ATTN_CHECK_CUDA(cudaMemcpyAsync(seg_start.p, hstart.data(), sizeof(int) * (size_t)(G + 1), cudaMemcpyHostToDevice, st));
+    pgrid = G;
   }
 };
 
@@ -582,6 +750,8 @@ static TcState* tc_build(attn_heff* h, bool tf) {
       t->y[k] = std::move(old->y[k]);
     }
     t->err = std::move(old->err);
+    t->segs = std::move(old->segs);
+    t->seg_start = std::move(old->seg_start);
     t->t0 = std::move(old->t0);
     t->t1 = std::move(old->t1);
     t->t2 = std::move(old->t2);
@@ -643,6 +813,11 @@ static TcState* tc_build(attn_heff* h, bool tf) {
   }
   t->prm.nkinds = nk;
   t->grid = cta;
+  t->prm.segs = nullptr;
+  t->prm.seg_start = nullptr;
+  t->tprm.segs = nullptr;
+  t->tprm.seg_start = nullptr;
+  if (nk > 0) t->build_segments(std::max(ctx->num_sms, 1), st);
   t->err.reserve(sizeof(int));
   ATTN_CHECK_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), st));
   t->prm.err = t->err.as<int>();
@@ -740,6 +915,22 @@ void attn_heff::apply_tc(const double* x, double* y, bool tf) {
       if (t->R[k]) ATTN_CHECK_CUDA(cudaMemsetAsync(t->y[k].p, 0, sizeof(float) * (size_t)V, st));
   };
   const std::array<int, 7> key = {m[0], m[1], m[2], t->R[0], t->R[1], t->R[2], tf ? 1 : 0};
+  const int sched = ctx->cfg.tc_schedule;
+  if (t->grid > 0 && sched == 2) {
+    // persistent form requested
+    if (!t->persistent || !t->tuned) t->set_split(0);
+    t->tuned = true;
+  } else if (t->grid > 0 && sched == 1 && (t->persistent || !t->tuned)) {
+    // split grid requested: the smallest split that gives every SM a CTA (no timing)
+    int f = 1;
+    for (int c : {1, 2, 3, 4, 6, 8}) {
+      t->set_split(c);
+      f = c;
+      if (t->grid >= ctx->num_sms) break;
+    }
+    t->set_split(f);
+    t->tuned = true;
+  }
   if (t->grid > 0 && !t->tuned) {
     auto hit = ctx->tc_split_cache.find(key);
     double fl_all = 0.0;
@@ -769,7 +960,7 @@ void attn_heff::apply_tc(const double* x, double* y, bool tf) {
     ATTN_CHECK_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     int best_f = 1;
-    for (int f : {1, 2, 3, 4, 5, 6, 8, 10, 12}) {
+    for (int f : {0, 1, 2, 3, 4, 5, 6, 8, 10, 12}) {
       t->set_split(f);
       if (f > 1 && !t->split_any()) continue;
       float tot = 0.f;

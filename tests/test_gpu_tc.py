@@ -36,15 +36,16 @@ def _case(shape, counts, seed, with_hint=True):
     return h, pairs
 
 
+@pytest.mark.parametrize("schedule", [1, 2])  # split grid, persistent
 @pytest.mark.parametrize("shape,counts", [
     ((128, 128, 128), (3, 2, 2)),
     ((64, 64, 64), (10, 6, 6)),
     ((16, 16, 128), (12, 8, 8)),
-    ((32, 48, 80), (5, 4, 3)),
+    ((32, 48, 80), (5, 4, 3)),       # kinds of different P: persistent runs cross kinds
     ((128, 128, 128), (0, 0, 5)),   # one kind only
 ])
-def test_bf16_heff_within_rounding_bound(shape, counts):
-    attn, ctx = lib_and_ctx()
+def test_bf16_heff_within_rounding_bound(shape, counts, schedule):
+    attn, ctx = lib_and_ctx({"tc_schedule": schedule})
     h, pairs = _case(shape, counts, seed=3)
     x = random_vector(shape, 9)
     H = attn.attn_heff_create(ctx, shape, [dev(a) for a in h], {k: (dev(a), dev(b)) for k, (a, b) in pairs.items()})
@@ -67,11 +68,12 @@ def test_bf16_heff_within_rounding_bound(shape, counts):
     attn.attn_destroy(ctx)
 
 
-def test_bf16_heff_full_size_many_products():
+@pytest.mark.parametrize("schedule", [0, 1, 2])  # timed choice, split grid, persistent
+def test_bf16_heff_full_size_many_products(schedule):
     """[128]^3 with ~300 products per kind (the size of the 32x32, m = 128 top nodes), sampled."""
     shape = (128, 128, 128)
     counts = (300, 120, 120)
-    attn, ctx = lib_and_ctx()
+    attn, ctx = lib_and_ctx({"tc_schedule": schedule})
     h, pairs = _case(shape, counts, seed=21)
     x = random_vector(shape, 4)
     H = attn.attn_heff_create(ctx, shape, [dev(a) for a in h], {k: (dev(a), dev(b)) for k, (a, b) in pairs.items()})
@@ -290,3 +292,35 @@ def test_bf16_heff_three_link_products_full_size_sampled():
     assert np.all(np.abs(got - ref) <= _bound3(shape, counts, nt) * absref)
     attn.attn_heff_destroy(H)
     attn.attn_destroy(ctx)
+
+
+def test_bf16_schedules_agree_to_fp32_rounding():
+    """The persistent form and the split grid sum the same BF16 products; only the FP32
+    summation order differs (where a slice pair's products are split between CTAs the
+    partial sums meet by atomics). Each order's FP32 error is at most (R P + Q + 2) 2^-24
+    of the summed magnitudes, so at sampled entries the two outputs differ by at most
+    twice that, with the magnitudes bounded by the same contraction of |x| and |operators|."""
+    import torch
+    shape, counts = (128, 128, 128), (290, 290, 290)
+    h, pairs = _case(shape, counts, seed=8)
+    x = random_vector(shape, 6)
+    out = {}
+    for schedule in (1, 2):
+        attn, ctx = lib_and_ctx({"tc_schedule": schedule})
+        H = attn.attn_heff_create(ctx, shape, [dev(a) for a in h], {k: (dev(a), dev(b)) for k, (a, b) in pairs.items()})
+        xd = dev(x)
+        yd = torch.empty_like(xd)
+        attn.attn_heff_apply(H, xd, yd, attn.ATTN_BF16)
+        out[schedule] = host(yd)
+        attn.attn_heff_destroy(H)
+        attn.attn_destroy(ctx)
+    op = {KINDS[k]: v for k, v in pairs.items()}
+    rng = np.random.default_rng(2)
+    idx = [tuple(int(v) for v in rng.integers(0, 128, 3)) for _ in range(16)]
+    absref = heff_sample_ops(np.abs(x), idx, tuple(np.abs(a) for a in h),
+                             {k: (np.abs(a), np.abs(b)) for k, (a, b) in op.items()})
+    R, P = max(counts) + 3, 128
+    bound = 2 * (R * P + P + 2) * 2.0 ** -24 * (1 + U) ** 4
+    diff = np.array([abs(out[1][i] - out[2][i]) for i in idx])
+    assert np.all(diff <= bound * absref), float((diff / absref).max())
+    assert np.isfinite(out[2]).all()

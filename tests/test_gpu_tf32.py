@@ -62,8 +62,9 @@ def _apply(attn, ctx, shape, h, pairs, trip, x, dtype, reps=1):
     ((64, 64, 64), (0, 0, 0), 12),     # three-link products only
     ((32, 48, 80), (5, 4, 3), 7),
 ])
-def test_tf32_heff_within_rounding_bound(shape, counts, nt):
-    attn, ctx = lib_and_ctx()
+@pytest.mark.parametrize("schedule", [1, 2])  # split grid, persistent (pair products)
+def test_tf32_heff_within_rounding_bound(shape, counts, nt, schedule):
+    attn, ctx = lib_and_ctx({"tc_schedule": schedule})
     h, pairs, trip = _case(shape, counts, nt, seed=3)
     x = random_vector(shape, 9)
     y = _apply(attn, ctx, shape, h, pairs, trip, x, attn.ATTN_TF32, reps=2)
