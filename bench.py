@@ -441,8 +441,12 @@ def run_sweeps(args):
     assert ref in ("f64", "f64_split"), "the first arm is the FP64 reference"
     for mode in modes:
         cfg = arm_config(attn, mode)
+        cfg.compress_terms = 1 if args.compress else 0
         ctx = attn.attn_create(cfg, torch.cuda.current_stream().cuda_stream)
-        model = attn.attn_model_tfim(ctx, Ls, h)
+        if args.model == "tri_heisenberg":
+            model = attn.attn_model_tri_heisenberg(ctx, Ls, 1.0)
+        else:
+            model = attn.attn_model_tfim(ctx, Ls, h)
         st = attn.attn_state_create(ctx, model, ms, raw)
         n_de = attn.attn_de_place(st, n // 4)
         if args.phases:
@@ -470,7 +474,8 @@ def run_sweeps(args):
     line = {"metric": "sweep time to dE/site<=1e-8, mixed vs FP64", "unit": "s",
             "value": out[head]["time_to_1e-8_s"], "value_arm": head, "higher_is_better": False,
             "f64_value": out[ref]["time_to_1e-8_s"], "final_energy_per_site_diff": d,
-            "config": {"workload": f"tfim{Ls}x{Ls}_m{ms}_sweeps", "L": Ls, "m": ms, "h": h,
+            "config": {"workload": f"{args.model}{Ls}x{Ls}_m{ms}_sweeps", "L": Ls, "m": ms,
+                       "coupling": 1.0 if args.model == "tri_heisenberg" else h, "compress_terms": bool(args.compress),
                        "s_ttn": 1, "lanczos_depth": 20,
                        "mixed": "bf16 Lanczos + <= 8 FP64 Rayleigh-Ritz corrections from 16-step bf16 CG "
                                 "Jacobi-Davidson solves, until theta moves by < 1e-10 |theta|",
@@ -888,6 +893,9 @@ def main():
                     choices=["matvec", "sweep", "nodes", "converge", "split", "sttn", "target", "oracle_sample"])
     ap.add_argument("--sweep-L", type=int, default=16)
     ap.add_argument("--sweep-m", type=int, default=32)
+    ap.add_argument("--model", default="tfim", choices=["tfim", "tri_heisenberg"],
+                    help="sweep mode: square-lattice TFIM (h = 3.04) or triangular-lattice Heisenberg (J = 1)")
+    ap.add_argument("--compress", action="store_true", help="sweep mode: compress mapped terms on the same sites")
     ap.add_argument("--max-sweeps", type=int, default=30)
     ap.add_argument("--prefix", type=int, default=3, help="FP64 aTTN sweeps before the frozen-layer runs")
     ap.add_argument("--arms", default="f64,mixed_k3,mixed,mixed_split",
