@@ -676,7 +676,8 @@ static void eigsolve_dev(attn_heff* h, double* T_dev, double* theta, int* iters)
       copy_f64(ctx, ctx->ws[3].as<double>(), T_dev, h->V);
       const bool prof_was = ctx->prof_on;
       ctx->prof_on = false;
-      lanczos_enqueue(ctx, lo, ctx->ws[3].as<double>(), h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0);
+      lanczos_enqueue(ctx, lo, ctx->ws[3].as<double>(), h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0,
+                      dt != ATTN_F64);
       ctx->prof_on = prof_was;
       ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
       g->epoch_before = ctx->scratch_epoch;
@@ -688,7 +689,7 @@ static void eigsolve_dev(attn_heff* h, double* T_dev, double* theta, int* iters)
       cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
       try {
         ATTN_CHECK_CUDA(ce);
-        lanczos_enqueue(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0);
+        lanczos_enqueue(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0, dt != ATTN_F64);
       } catch (...) {
         cudaGraph_t tmp = nullptr;
         cudaStreamEndCapture(cs, &tmp);
@@ -742,7 +743,7 @@ static void eigsolve_dev(attn_heff* h, double* T_dev, double* theta, int* iters)
   }
   LanczosWork w;
   LanczosResult r = timeout_first(ctx, h, [&] {
-    return lanczos_lowest(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, w);
+    return lanczos_lowest(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, w, dt != ATTN_F64);
   });
   double th = r.theta;
   int it = r.iters;

@@ -22,6 +22,7 @@
 // the result once.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "attn_internal.h"
 #include "lanczos.h"
@@ -44,6 +45,10 @@ __device__ __forceinline__ long bidx(int i, long e, long V, int D) {
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
@@ -110,14 +115,15 @@ __global__ void multi_axpy(double* w, const double* basis, const double* coef, i
 constexpr int kFusedMax = 24;
 
 // Sum the per-thread values acc[0..n) over the block and write them to out[0..n).
-template <int NV>
-__device__ __forceinline__ void block_sum_store(double (&acc)[NV], int n, double* out) {
+// (warp sums in the accumulator's type, the rest in FP64)
+template <int NV, class A>
+__device__ __forceinline__ void block_sum_store(A (&acc)[NV], int n, double* out) {
   __shared__ double sh[LT / 32][NV];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     if (i < n) {
-      const double s = warp_sum(acc[i]);
+      const double s = (double)warp_sum(acc[i]);
       if (lane == 0) sh[warp][i] = s;
     }
   }
@@ -129,19 +135,23 @@ __device__ __forceinline__ void block_sum_store(double (&acc)[NV], int n, double
   }
 }
 
+// The passes are instantiated for an FP64 basis and for an FP32 one (the basis of a
+// Lanczos whose matvecs run in BF16 or TF32: its vectors carry no more than FP32 accuracy);
+// they compute in the basis' type T, with w (FP64 storage) rounded to T on load.
+
 // (A) part[b][i] = block b's share of <basis_i, w>
-template <int NV, int U>
-__global__ void __launch_bounds__(LT, 2) cgs_dot(const double* __restrict__ basis, int n, long V, int D,
+template <int NV, int U, class T>
+__global__ void __launch_bounds__(LT, 2) cgs_dot(const T* __restrict__ basis, int n, long V, int D,
                                               const double* __restrict__ w, double* part, const double* done) {
   if (done && *done != 0.0) return;
-  double acc[NV];
+  T acc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (int i = 0; i < NV; ++i) acc[i] = 0;
   const long stride = (long)gridDim.x * LT;
   for (long e0 = blockIdx.x * (long)LT + threadIdx.x; e0 < V; e0 += stride * U) {
-    double we[U];
+    T we[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) we[u] = (e0 + u * stride < V) ? w[e0 + u * stride] : 0.0;
+    for (int u = 0; u < U; ++u) we[u] = (e0 + u * stride < V) ? (T)w[e0 + u * stride] : (T)0;
 #pragma unroll
     for (int i = 0; i < NV; ++i)
       if (i < n) {
@@ -154,34 +164,34 @@ __global__ void __launch_bounds__(LT, 2) cgs_dot(const double* __restrict__ basi
 }
 
 // (B) w -= sum_i h_i basis_i, then part[b][i] = block share of <basis_i, w_new>
-template <int NV, int U>
-__global__ void __launch_bounds__(LT, 2) cgs_axpy_dot(double* __restrict__ w, const double* __restrict__ basis,
+template <int NV, int U, class T>
+__global__ void __launch_bounds__(LT, 2) cgs_axpy_dot(double* __restrict__ w, const T* __restrict__ basis,
                                                    const double* h, int n, long V, int D, double* part,
                                                    const double* done) {
   if (done && *done != 0.0) return;
-  __shared__ double c[NV];
-  if (threadIdx.x < NV) c[threadIdx.x] = threadIdx.x < n ? h[threadIdx.x] : 0.0;
+  __shared__ T c[NV];
+  if (threadIdx.x < NV) c[threadIdx.x] = threadIdx.x < n ? (T)h[threadIdx.x] : (T)0;
   __syncthreads();
-  double acc[NV];
+  T acc[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+  for (int i = 0; i < NV; ++i) acc[i] = 0;
   const long stride = (long)gridDim.x * LT;
   if constexpr (NV == 16 || NV == 20) {
     // wide bases: each thread parks the basis elements it loads for the update of w in
     // its own column of shared memory and reads them back for the dot products, so that
     // only the accumulators stay in registers and two blocks fit on an SM
     static_assert(U == 1, "the shared-memory form handles one element per thread and pass");
-    __shared__ double sb[NV][LT];
+    __shared__ T sb[NV][LT];
     for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += stride) {
-      double v = w[e];
+      T v = (T)w[e];
 #pragma unroll
       for (int i = 0; i < NV; ++i)
         if (i < n) {
-          const double bi = basis[bidx(i, e, V, D)];
+          const T bi = basis[bidx(i, e, V, D)];
           sb[i][threadIdx.x] = bi;
           v = fma(-c[i], bi, v);
         }
-      w[e] = v;
+      w[e] = (double)v;
 #pragma unroll
       for (int i = 0; i < NV; ++i)
         if (i < n) acc[i] = fma(sb[i][threadIdx.x], v, acc[i]);
@@ -190,13 +200,13 @@ __global__ void __launch_bounds__(LT, 2) cgs_axpy_dot(double* __restrict__ w, co
     return;
   }
   for (long e0 = blockIdx.x * (long)LT + threadIdx.x; e0 < V; e0 += stride * U) {
-    double b[U][NV], v[U];
+    T b[U][NV], v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const long e = e0 + u * stride;
-      v[u] = e < V ? w[e] : 0.0;
+      v[u] = e < V ? (T)w[e] : (T)0;
 #pragma unroll
-      for (int i = 0; i < NV; ++i) b[u][i] = (i < n && e < V) ? basis[bidx(i, e, V, D)] : 0.0;
+      for (int i = 0; i < NV; ++i) b[u][i] = (i < n && e < V) ? basis[bidx(i, e, V, D)] : (T)0;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -204,7 +214,7 @@ __global__ void __launch_bounds__(LT, 2) cgs_axpy_dot(double* __restrict__ w, co
       for (int i = 0; i < NV; ++i)
         if (i < n) v[u] = fma(-c[i], b[u][i], v[u]);
       const long e = e0 + u * stride;
-      if (e < V) w[e] = v[u];
+      if (e < V) w[e] = (double)v[u];
 #pragma unroll
       for (int i = 0; i < NV; ++i)
         if (i < n) acc[i] = fma(b[u][i], v[u], acc[i]);
@@ -214,20 +224,20 @@ __global__ void __launch_bounds__(LT, 2) cgs_axpy_dot(double* __restrict__ w, co
 }
 
 // (C) w -= sum_i h_i basis_i, then part[b] = block share of ||w_new||^2
-template <int NV, int U>
-__global__ void __launch_bounds__(LT, 2) cgs_axpy_norm(double* __restrict__ w, const double* __restrict__ basis,
+template <int NV, int U, class T>
+__global__ void __launch_bounds__(LT, 2) cgs_axpy_norm(double* __restrict__ w, const T* __restrict__ basis,
                                                     const double* h, int n, long V, int D, double* part,
                                                     const double* done) {
   if (done && *done != 0.0) return;
-  __shared__ double c[NV];
-  if (threadIdx.x < NV) c[threadIdx.x] = threadIdx.x < n ? h[threadIdx.x] : 0.0;
+  __shared__ T c[NV];
+  if (threadIdx.x < NV) c[threadIdx.x] = threadIdx.x < n ? (T)h[threadIdx.x] : (T)0;
   __syncthreads();
-  double acc[1] = {0.0};
+  T acc[1] = {0};
   const long stride = (long)gridDim.x * LT;
   for (long e0 = blockIdx.x * (long)LT + threadIdx.x; e0 < V; e0 += stride * U) {
-    double v[U];
+    T v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = (e0 + u * stride < V) ? w[e0 + u * stride] : 0.0;
+    for (int u = 0; u < U; ++u) v[u] = (e0 + u * stride < V) ? (T)w[e0 + u * stride] : (T)0;
 #pragma unroll
     for (int i = 0; i < NV; ++i)
       if (i < n) {
@@ -238,7 +248,7 @@ __global__ void __launch_bounds__(LT, 2) cgs_axpy_norm(double* __restrict__ w, c
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (e0 + u * stride < V) {
-        w[e0 + u * stride] = v[u];
+        w[e0 + u * stride] = (double)v[u];
         acc[0] = fma(v[u], v[u], acc[0]);
       }
   }
@@ -246,12 +256,13 @@ __global__ void __launch_bounds__(LT, 2) cgs_axpy_norm(double* __restrict__ w, c
 }
 
 // out = sum_{i < n} coef[i] * basis_i with n = nvec, or (int)*nvec_dev if given
-__global__ void combine(double* out, const double* basis, const double* coef, int nvec, const double* nvec_dev,
+template <class T>
+__global__ void combine(double* out, const T* basis, const double* coef, int nvec, const double* nvec_dev,
                         long V, int D) {
   const int n = nvec_dev ? (int)(*nvec_dev) : nvec;
   for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) {
     double v = 0.0;
-    for (int i = 0; i < n; ++i) v = fma(coef[i], basis[bidx(i, e, V, D)], v);
+    for (int i = 0; i < n; ++i) v = fma(coef[i], (double)basis[bidx(i, e, V, D)], v);
     out[e] = v;
   }
 }
@@ -265,15 +276,18 @@ __global__ void scale_by_norm(double* dst, const double* src, const double* nrm_
 }
 
 // The same into slot i of the interleaved basis (capacity D) and into the contiguous vk.
-__global__ void scale_into_basis(double* basis, int i, int D, double* vk, const double* src, const double* nrm_sq,
+// basis_i = src / ||src|| (in the basis' type) and vk = the same vector in FP64, so that the
+// next matvec sees exactly the stored basis vector.
+template <class T>
+__global__ void scale_into_basis(T* basis, int i, int D, double* vk, const double* src, const double* nrm_sq,
                                  long V, const double* done) {
   if (done && *done != 0.0) return;
   double n = sqrt(*nrm_sq);
   double inv = n > 0.0 ? 1.0 / n : 0.0;
   for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) {
-    const double v = src[e] * inv;
+    const T v = (T)(src[e] * inv);
     basis[bidx(i, e, V, D)] = v;
-    vk[e] = v;
+    vk[e] = (double)v;
   }
 }
 
@@ -424,26 +438,27 @@ __global__ void lz_init(double* S) {
 
 inline int vgrid(long V) { return (int)std::max<long>(1, std::min<long>((V + LT - 1) / LT, LB)); }
 
-template <int NV, int U>
-void cgs2_launch(cudaStream_t s, const double* B, int D, double* W, double* S, int n, long V, int nb, double* part,
+template <int NV, int U, class T>
+void cgs2_launch(cudaStream_t s, const T* B, int D, double* W, double* S, int n, long V, int nb, double* part,
                  const double* done) {
-  cgs_dot<NV, U><<<nb, LT, 0, s>>>(B, n, V, D, W, part, done);
+  cgs_dot<NV, U, T><<<nb, LT, 0, s>>>(B, n, V, D, W, part, done);
   multi_dot_reduce<<<n, LT, 0, s>>>(part, nb, n, S + S_H, nullptr, done);
-  cgs_axpy_dot<NV, U><<<nb, LT, 0, s>>>(W, B, S + S_H, n, V, D, part, done);
+  cgs_axpy_dot<NV, U, T><<<nb, LT, 0, s>>>(W, B, S + S_H, n, V, D, part, done);
   multi_dot_reduce<<<n, LT, 0, s>>>(part, nb, n, S + S_H2, nullptr, done);
-  cgs_axpy_norm<NV, U><<<nb, LT, 0, s>>>(W, B, S + S_H2, n, V, D, part, done);
+  cgs_axpy_norm<NV, U, T><<<nb, LT, 0, s>>>(W, B, S + S_H2, n, V, D, part, done);
   multi_dot_reduce<<<1, LT, 0, s>>>(part, nb, 1, S + S_TMP, nullptr, done);
 }
 
 // One CGS2 step against n <= kFusedMax basis vectors (six launches).
-void cgs2_fused(cudaStream_t s, const double* B, int D, double* W, double* S, int n, long V, int nb, double* part,
+template <class T>
+void cgs2_fused(cudaStream_t s, const T* B, int D, double* W, double* S, int n, long V, int nb, double* part,
                 const double* done) {
-  if (n <= 4) cgs2_launch<4, 4>(s, B, D, W, S, n, V, nb, part, done);
-  else if (n <= 8) cgs2_launch<8, 2>(s, B, D, W, S, n, V, nb, part, done);
-  else if (n <= 12) cgs2_launch<12, 2>(s, B, D, W, S, n, V, nb, part, done);
-  else if (n <= 16) cgs2_launch<16, 1>(s, B, D, W, S, n, V, nb, part, done);
-  else if (n <= 20) cgs2_launch<20, 1>(s, B, D, W, S, n, V, nb, part, done);
-  else cgs2_launch<24, 1>(s, B, D, W, S, n, V, nb, part, done);
+  if (n <= 4) cgs2_launch<4, 4, T>(s, B, D, W, S, n, V, nb, part, done);
+  else if (n <= 8) cgs2_launch<8, 2, T>(s, B, D, W, S, n, V, nb, part, done);
+  else if (n <= 12) cgs2_launch<12, 2, T>(s, B, D, W, S, n, V, nb, part, done);
+  else if (n <= 16) cgs2_launch<16, 1, T>(s, B, D, W, S, n, V, nb, part, done);
+  else if (n <= 20) cgs2_launch<20, 1, T>(s, B, D, W, S, n, V, nb, part, done);
+  else cgs2_launch<24, 1, T>(s, B, D, W, S, n, V, nb, part, done);
 }
 
 // Blocks for the fused streaming passes: enough resident warps on every SM to
@@ -482,7 +497,7 @@ void multi_axpy_dev(attn_ctx* ctx, double* w, const double* basis, const double*
 }
 
 void combine_dev(attn_ctx* ctx, double* out, const double* basis, const double* coef, int nvec, long V) {
-  combine<<<vgrid(V), LT, 0, ctx->stream>>>(out, basis, coef, nvec, nullptr, V, 0);
+  combine<double><<<vgrid(V), LT, 0, ctx->stream>>>(out, basis, coef, nvec, nullptr, V, 0);
   ctx->launches++;
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
@@ -494,16 +509,17 @@ void normalise_dev(attn_ctx* ctx, double* dst, const double* src, long V, double
   ATTN_CHECK_CUDA(cudaGetLastError());
 }
 
-void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol, LanczosWork& w,
-                     int host_check_every) {
+template <class T>
+void lanczos_enqueue_t(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol, LanczosWork& w,
+                       int host_check_every) {
   ATTN_REQUIRE(depth >= 1 && depth <= 60, ATTN_EINVAL, "Lanczos depth must be in 1..60");
   const int D = depth + 1;                 // basis capacity
   const long chunks = (V + LT - 1) / LT;   // interleaving granule: LT elements
-  w.basis.reserve(sizeof(double) * (size_t)D * chunks * LT);
+  w.basis.reserve(sizeof(T) * (size_t)D * chunks * LT);
   w.wvec.reserve(sizeof(double) * (size_t)V);
   w.vk.reserve(sizeof(double) * (size_t)V);
   w.scal.reserve(sizeof(double) * S_SIZE);
-  double* B = w.basis.as<double>();
+  T* B = w.basis.as<T>();
   double* W = w.wvec.as<double>();
   double* vk = w.vk.as<double>();
   double* S = w.scal.as<double>();
@@ -513,7 +529,7 @@ void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int 
   ctx->launches++;
   // v_0 = x / |x| into basis slot 0 and the contiguous matvec input
   multi_dot_g(ctx, x, 1, V, 0, x, S + S_TMP, nullptr, nullptr);
-  scale_into_basis<<<vgrid(V), LT, 0, s>>>(B, 0, D, vk, x, S + S_TMP, V, nullptr);
+  scale_into_basis<T><<<vgrid(V), LT, 0, s>>>(B, 0, D, vk, x, S + S_TMP, V, nullptr);
   ctx->launches++;
   for (int k = 0; k < depth; ++k) {
     apply(vk, W);
@@ -524,9 +540,9 @@ void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int 
     if (n <= kFusedMax) {
       const int nb = fused_grid(V);
       ctx->partials.reserve(sizeof(double) * (size_t)nb * n);
-      cgs2_fused(s, B, D, W, S, n, V, nb, ctx->partials.as<double>(), done);
+      cgs2_fused<T>(s, B, D, W, S, n, V, nb, ctx->partials.as<double>(), done);
       ctx->launches += 6;
-    } else {
+    } else if constexpr (std::is_same<T, double>::value) {
       multi_dot_g(ctx, B, n, V, D, W, S + S_H, nullptr, done);
       multi_axpy<<<vgrid(V), LT, 0, s>>>(W, B, S + S_H, n, V, D, 1.0, done);
       multi_dot_g(ctx, B, n, V, D, W, S + S_H2, nullptr, done);
@@ -537,7 +553,7 @@ void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int 
     lz_step<<<1, 32, 0, s>>>(S, k, depth, tol);
     ctx->launches++;
     if (k + 1 < depth) {
-      scale_into_basis<<<vgrid(V), LT, 0, s>>>(B, k + 1, D, vk, W, S + S_TMP, V, done);
+      scale_into_basis<T><<<vgrid(V), LT, 0, s>>>(B, k + 1, D, vk, W, S + S_TMP, V, done);
       ctx->launches++;
     }
     if (host_check_every > 0 && (k + 1) % host_check_every == 0 && k + 1 < depth) {
@@ -547,10 +563,17 @@ void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int 
       if (hd != 0.0) break;
     }
   }
-  combine<<<vgrid(V), LT, 0, s>>>(W, B, S + S_Y, 0, S + S_NK, V, D);
+  combine<T><<<vgrid(V), LT, 0, s>>>(W, B, S + S_Y, 0, S + S_NK, V, D);
   ctx->launches++;
   normalise_dev(ctx, x, W, V, S + S_TMP);
   ATTN_CHECK_CUDA(cudaGetLastError());
+}
+
+void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol, LanczosWork& w,
+                     int host_check_every, bool f32_basis) {
+  // the FP32 basis keeps every step in the fused passes
+  if (f32_basis && depth <= kFusedMax) lanczos_enqueue_t<float>(ctx, apply, x, V, depth, tol, w, host_check_every);
+  else lanczos_enqueue_t<double>(ctx, apply, x, V, depth, tol, w, host_check_every);
 }
 
 LanczosResult lanczos_read(attn_ctx* ctx, LanczosWork& w) {
@@ -564,8 +587,8 @@ LanczosResult lanczos_read(attn_ctx* ctx, LanczosWork& w) {
 }
 
 LanczosResult lanczos_lowest(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol,
-                             LanczosWork& w) {
-  lanczos_enqueue(ctx, apply, x, V, depth, tol, w, tol > 0.0 ? 5 : 0);
+                             LanczosWork& w, bool f32_basis) {
+  lanczos_enqueue(ctx, apply, x, V, depth, tol, w, tol > 0.0 ? 5 : 0, f32_basis);
   LanczosResult r = lanczos_read(ctx, w);
   r.converged = r.resid < tol * std::max(std::fabs(r.theta), 1e-300);
   return r;

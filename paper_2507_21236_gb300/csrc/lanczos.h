@@ -22,13 +22,16 @@ struct LanczosResult {
 };
 
 // Lowest Ritz pair of the symmetric operator `apply` starting from x (device,
-// length V). On return x holds the unit-norm Ritz vector.
+// length V). On return x holds the unit-norm Ritz vector. f32_basis: keep the Krylov
+// basis and its reorthogonalisation in FP32 (for a low-precision `apply`, whose
+// vectors carry no more; depth <= 24, else FP64 is used); the recurrence scalars,
+// the matvec input and output and the Ritz vector stay FP64.
 LanczosResult lanczos_lowest(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol,
-                             LanczosWork& w);
+                             LanczosWork& w, bool f32_basis = false);
 // The same as a fixed launch sequence with no host synchronisation when
 // host_check_every == 0 (capturable); lanczos_read waits and returns the result.
 void lanczos_enqueue(attn_ctx* ctx, const MatVec& apply, double* x, long V, int depth, double tol, LanczosWork& w,
-                     int host_check_every);
+                     int host_check_every, bool f32_basis = false);
 LanczosResult lanczos_read(attn_ctx* ctx, LanczosWork& w);
 
 // Mixed-precision refinement of the lowest eigenpair after a low-precision
