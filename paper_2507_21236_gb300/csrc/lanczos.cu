@@ -48,6 +48,10 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
+// fused multiply-add in the operands' own precision (never promoted)
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(LT, 2) cgs_dot(const T* __restrict__ basis, in
       if (i < n) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (e0 + u * stride < V) acc[i] = fma(basis[bidx(i, e0 + u * stride, V, D)], we[u], acc[i]);
+          if (e0 + u * stride < V) acc[i] = fma_t(basis[bidx(i, e0 + u * stride, V, D)], we[u], acc[i]);
       }
   }
   block_sum_store<NV>(acc, n, part + (long)blockIdx.x * n);
@@ -189,12 +193,12 @@ __global__ void __launch_bounds__(LT, 2) cgs_axpy_dot(double* __restrict__ w, co
         if (i < n) {
           const T bi = basis[bidx(i, e, V, D)];
           sb[i][threadIdx.x] = bi;
-          v = fma(-c[i], bi, v);
+          v = fma_t(-c[i], bi, v);
         }
       w[e] = (double)v;
 #pragma unroll
       for (int i = 0; i < NV; ++i)
-        if (i < n) acc[i] = fma(sb[i][threadIdx.x], v, acc[i]);
+        if (i < n) acc[i] = fma_t(sb[i][threadIdx.x], v, acc[i]);
     }
     block_sum_store<NV>(acc, n, part + (long)blockIdx.x * n);
     return;
@@ -212,12 +216,12 @@ __global__ void __launch_bounds__(LT, 2) cgs_axpy_dot(double* __restrict__ w, co
     for (int u = 0; u < U; ++u) {
 #pragma unroll
       for (int i = 0; i < NV; ++i)
-        if (i < n) v[u] = fma(-c[i], b[u][i], v[u]);
+        if (i < n) v[u] = fma_t(-c[i], b[u][i], v[u]);
       const long e = e0 + u * stride;
       if (e < V) w[e] = (double)v[u];
 #pragma unroll
       for (int i = 0; i < NV; ++i)
-        if (i < n) acc[i] = fma(b[u][i], v[u], acc[i]);
+        if (i < n) acc[i] = fma_t(b[u][i], v[u], acc[i]);
     }
   }
   block_sum_store<NV>(acc, n, part + (long)blockIdx.x * n);
@@ -243,13 +247,13 @@ __global__ void __launch_bounds__(LT, 2) cgs_axpy_norm(double* __restrict__ w, c
       if (i < n) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (e0 + u * stride < V) v[u] = fma(-c[i], basis[bidx(i, e0 + u * stride, V, D)], v[u]);
+          if (e0 + u * stride < V) v[u] = fma_t(-c[i], basis[bidx(i, e0 + u * stride, V, D)], v[u]);
       }
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (e0 + u * stride < V) {
         w[e0 + u * stride] = (double)v[u];
-        acc[0] = fma(v[u], v[u], acc[0]);
+        acc[0] = fma_t(v[u], v[u], acc[0]);
       }
   }
   block_sum_store<1>(acc, 1, part + blockIdx.x);
@@ -262,7 +266,7 @@ __global__ void combine(double* out, const T* basis, const double* coef, int nve
   const int n = nvec_dev ? (int)(*nvec_dev) : nvec;
   for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) {
     double v = 0.0;
-    for (int i = 0; i < n; ++i) v = fma(coef[i], (double)basis[bidx(i, e, V, D)], v);
+    for (int i = 0; i < n; ++i) v = fma_t(coef[i], (double)basis[bidx(i, e, V, D)], v);
     out[e] = v;
   }
 }
