@@ -845,10 +845,10 @@ def run_nodes(args):
         y64 = torch.empty_like(x)
         attn.attn_heff_apply(H, x.data_ptr(), y64.data_ptr(), attn.ATTN_F64)
         errs = {}
-        for name, dt in (("bf16", attn.ATTN_BF16), ("tf32", attn.ATTN_TF32)):
+        for dname, dt in (("bf16", attn.ATTN_BF16), ("tf32", attn.ATTN_TF32)):
             attn.attn_heff_apply(H, x.data_ptr(), y.data_ptr(), dt)
             torch.cuda.synchronize()
-            errs[name] = float((y - y64).abs().max() / y64.abs().max())
+            errs[dname] = float((y - y64).abs().max() / y64.abs().max())
         # the same FP64 applications with the contractions as exact BF16 slice products
         cfg = attn.attn_get_config(ctx)
         cfg.f64_split = 1
