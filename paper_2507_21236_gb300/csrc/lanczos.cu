@@ -259,15 +259,27 @@ __global__ void __launch_bounds__(LT, 2) cgs_axpy_norm(double* __restrict__ w, c
   block_sum_store<1>(acc, 1, part + blockIdx.x);
 }
 
-// out = sum_{i < n} coef[i] * basis_i with n = nvec, or (int)*nvec_dev if given
+// out = sum_{i < n} coef[i] * basis_i with n = nvec, or (int)*nvec_dev if given; an FP32
+// basis (at most 61 vectors) is summed in FP32, since it gives the vector no more accuracy
 template <class T>
 __global__ void combine(double* out, const T* basis, const double* coef, int nvec, const double* nvec_dev,
                         long V, int D) {
   const int n = nvec_dev ? (int)(*nvec_dev) : nvec;
-  for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) {
-    double v = 0.0;
-    for (int i = 0; i < n; ++i) v = fma_t(coef[i], (double)basis[bidx(i, e, V, D)], v);
-    out[e] = v;
+  if constexpr (std::is_same<T, float>::value) {
+    __shared__ float c[64];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) c[i] = i < n ? (float)coef[i] : 0.0f;
+    __syncthreads();
+    for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) {
+      float v = 0.0f;
+      for (int i = 0; i < n && i < 64; ++i) v = fma_t(c[i], basis[bidx(i, e, V, D)], v);
+      out[e] = (double)v;
+    }
+  } else {
+    for (long e = blockIdx.x * (long)LT + threadIdx.x; e < V; e += (long)gridDim.x * LT) {
+      double v = 0.0;
+      for (int i = 0; i < n; ++i) v = fma_t(coef[i], basis[bidx(i, e, V, D)], v);
+      out[e] = v;
+    }
   }
 }
 
