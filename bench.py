@@ -1015,6 +1015,30 @@ def main():
 
     # the accuracy-bearing form of the same solve: BF16 Lanczos then FP64 Rayleigh-Ritz
     # refinement (3 Jacobi-Davidson corrections, FP64 contractions as split BF16 products)
+    # the same timed loop with the optional FP32 Krylov basis (lanczos_basis = 1): the
+    # reorthogonalisation in FP32 instead of FP64 (not the default precision policy)
+    cfg_b = attn.attn_get_config(ctx)
+    cfg_b.lanczos_basis = 1
+    attn.attn_set_config(ctx, cfg_b)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs_b, it_b = [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        it_b += step()
+        b.record(stream)
+        evs_b.append((a, b))
+    torch.cuda.synchronize()
+    ms_b = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs_b), world, "cuda")
+    cfg_b.lanczos_basis = 0
+    attn.attn_set_config(ctx, cfg_b)
+    f32_basis = {"value": whole_job_rate(it_b, world, ms_b), "unit": "matvec/s", "ms_per_step": ms_b / args.steps,
+                 "config": "lanczos_basis = 1: Krylov basis and CGS2 reorthogonalisation in FP32 (recurrence "
+                           "scalars, matvec vectors and Ritz vector FP64); an option, not the default policy"}
+
     solve = None if args.no_solve else mixed_solve_record(attn, ctx, H, x0, torch)
 
     peaks, src = measured_peaks()
@@ -1039,7 +1063,7 @@ def main():
                        "l2": "256 MB buffer written between timed steps; Lanczos basis 336 MB > L2",
                        "parallelism": f"replicas{world}"},
             "roofline": roof, "gpu_launches": int(launches), "e2e": e2e, "clocks": clk.summary(),
-            "mixed_solve": solve}
+            "mixed_solve": solve, "fp32_krylov_basis": f32_basis}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(oracle_node_structure())
     if rank == 0 and world == 1 and not args.no_sweep:

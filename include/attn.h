@@ -108,6 +108,11 @@ typedef struct {
                                split grid (one CTA per slice pair and product range), 2 = persistent (one CTA per
                                SM over a cost-balanced cut of the node's products). Results agree to FP32
                                rounding either way (0) */
+  int lanczos_basis;        /* Krylov basis and CGS2 reorthogonalisation of a Lanczos with BF16 or TF32 matvecs:
+                               0 = FP64 (the Lanczos recurrence, its reorthogonalisation and the Ritz solve all
+                               in FP64), 1 = FP32 basis and FP32 reorthogonalisation (recurrence scalars, matvec
+                               vectors and Ritz vector stay FP64; depth <= 24; a faster option whose vectors
+                               carry FP32 accuracy, which the FP64 refinement then lifts) (0) */
 } attn_config;
 
 ATTN_API attn_status attn_config_default(attn_config* cfg);

@@ -33,7 +33,8 @@ class attn_config(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("refine_inner", ctypes.c_int),
                 ("f64_split", ctypes.c_int), ("report_unconverged", ctypes.c_int),
                 ("wait_limit_log2", ctypes.c_int), ("compress_terms", ctypes.c_int),
-                ("de_method", ctypes.c_int), ("tc_schedule", ctypes.c_int)]
+                ("de_method", ctypes.c_int), ("tc_schedule", ctypes.c_int),
+                ("lanczos_basis", ctypes.c_int)]
 
 
 class attn_heff_desc(ctypes.Structure):

@@ -223,6 +223,7 @@ ATTN_API attn_status attn_set_config(attn_ctx* ctx, const attn_config* cfg) {
   ATTN_REQUIRE(cfg->wait_limit_log2 >= 0 && cfg->wait_limit_log2 <= 62, ATTN_EINVAL, "wait_limit_log2 must be 0..62");
   ATTN_REQUIRE(cfg->de_method == 0 || cfg->de_method == 1, ATTN_EINVAL, "de_method must be 0 or 1");
   ATTN_REQUIRE(cfg->tc_schedule >= 0 && cfg->tc_schedule <= 2, ATTN_EINVAL, "tc_schedule must be 0, 1 or 2");
+  ATTN_REQUIRE(cfg->lanczos_basis == 0 || cfg->lanczos_basis == 1, ATTN_EINVAL, "lanczos_basis must be 0 or 1");
   ctx->cfg = *cfg;
   ATTN_CATCH
 }
@@ -659,7 +660,8 @@ static void eigsolve_dev(attn_heff* h, double* T_dev, double* theta, int* iters)
     // (f64_split) or of the tensor-core grid (tc_schedule) makes it stale
     if (!g || g->x != T_dev || g->depth != cfg.lanczos_depth || g->tol != cfg.lanczos_tol || g->dtype != dt ||
         g->refine != rsteps || g->rtol != cfg.refine_tol || g->prof != ctx->prof_on ||
-        g->f64_split != cfg.f64_split || g->tc_schedule != cfg.tc_schedule || g->epoch != ctx->scratch_epoch) {
+        g->f64_split != cfg.f64_split || g->tc_schedule != cfg.tc_schedule || g->basis != cfg.lanczos_basis ||
+        g->epoch != ctx->scratch_epoch) {
       delete g;
       g = h->eg = new EigGraph();
       g->x = T_dev;
@@ -671,13 +673,14 @@ static void eigsolve_dev(attn_heff* h, double* T_dev, double* theta, int* iters)
       g->prof = ctx->prof_on;
       g->f64_split = cfg.f64_split;
       g->tc_schedule = cfg.tc_schedule;
+      g->basis = cfg.lanczos_basis;
       // warm-up on a scratch copy: every buffer the solve needs is allocated before capture
       ctx->ws[3].reserve(sizeof(double) * h->V);
       copy_f64(ctx, ctx->ws[3].as<double>(), T_dev, h->V);
       const bool prof_was = ctx->prof_on;
       ctx->prof_on = false;
       lanczos_enqueue(ctx, lo, ctx->ws[3].as<double>(), h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0,
-                      dt != ATTN_F64);
+                      dt != ATTN_F64 && cfg.lanczos_basis == 1);
       ctx->prof_on = prof_was;
       ATTN_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
       g->epoch_before = ctx->scratch_epoch;
@@ -689,7 +692,8 @@ static void eigsolve_dev(attn_heff* h, double* T_dev, double* theta, int* iters)
       cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
       try {
         ATTN_CHECK_CUDA(ce);
-        lanczos_enqueue(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0, dt != ATTN_F64);
+        lanczos_enqueue(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, g->w, 0,
+                        dt != ATTN_F64 && cfg.lanczos_basis == 1);
       } catch (...) {
         cudaGraph_t tmp = nullptr;
         cudaStreamEndCapture(cs, &tmp);
@@ -743,7 +747,8 @@ static void eigsolve_dev(attn_heff* h, double* T_dev, double* theta, int* iters)
   }
   LanczosWork w;
   LanczosResult r = timeout_first(ctx, h, [&] {
-    return lanczos_lowest(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, w, dt != ATTN_F64);
+    return lanczos_lowest(ctx, lo, T_dev, h->V, cfg.lanczos_depth, cfg.lanczos_tol, w,
+                          dt != ATTN_F64 && cfg.lanczos_basis == 1);
   });
   double th = r.theta;
   int it = r.iters;

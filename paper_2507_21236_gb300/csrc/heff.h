@@ -10,7 +10,7 @@ struct EigGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   const double* x = nullptr;
-  int depth = 0, dtype = 0, refine = 0, f64_split = 0, tc_schedule = 0;
+  int depth = 0, dtype = 0, refine = 0, f64_split = 0, tc_schedule = 0, basis = 0;
   double tol = 0.0, rtol = 0.0;
   bool prof = false;
   uint64_t epoch = ~0ull;         // the context's scratch_epoch the graph was captured under

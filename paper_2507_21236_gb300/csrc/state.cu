@@ -488,7 +488,8 @@ double attn_state::local_step(int n) {
     ctx->prof_begin(6);
     LanczosResult r =
         timeout_first(ctx, h, [&] {
-          return lanczos_lowest(ctx, mv_lo, v, V, cfg.lanczos_depth, cfg.lanczos_tol, lw, dt != ATTN_F64);
+          return lanczos_lowest(ctx, mv_lo, v, V, cfg.lanczos_depth, cfg.lanczos_tol, lw,
+                                dt != ATTN_F64 && cfg.lanczos_basis == 1);
         });
     ctx->prof_end(6, 0.0);
     double theta = r.theta;

@@ -62,4 +62,4 @@ def test_config_struct_layout_matches_the_header():
     assert (cfg.matvec_dtype, cfg.refine_steps, cfg.refine_tol, cfg.use_graphs, cfg.refine_inner, cfg.f64_split) == \
         (attn.ATTN_F64, 3, 1e-10, 0, 16, 0)
     # the C memset covers the whole struct: the zeroed tail reaches the binding's size
-    assert all(b == 0 for b in raw[end:n]) and (cfg.de_method, cfg.tc_schedule) == (0, 0)
+    assert all(b == 0 for b in raw[end:n]) and (cfg.de_method, cfg.tc_schedule, cfg.lanczos_basis) == (0, 0, 0)

@@ -324,3 +324,50 @@ def test_bf16_schedules_agree_to_fp32_rounding():
     diff = np.array([abs(out[1][i] - out[2][i]) for i in idx])
     assert np.all(diff <= bound * absref), float((diff / absref).max())
     assert np.isfinite(out[2]).all()
+
+
+@pytest.mark.parametrize("basis", [0, 1])  # FP64, FP32 Krylov basis
+def test_refined_eigsolve_with_either_krylov_basis(basis):
+    """A BF16 Lanczos with an FP64 or (lanczos_basis = 1) an FP32 Krylov basis and FP32
+    reorthogonalisation, followed by five FP64 Jacobi-Davidson corrections with BF16 inner
+    solves, reaches the converged FP64 eigenpair of a physical H_eff (8x8 TFIM, m = 32, top
+    node) to 1e-11 in theta; the returned value is the FP64 Rayleigh quotient of the
+    returned vector. Without refinement both bases give theta to BF16 accuracy."""
+    from inputs import raw_tree_tensors
+    from oracle.tree import Tree
+    import torch
+
+    attn, ctx = lib_and_ctx()
+    tree = Tree(64, 32)
+    model = attn.attn_model_tfim(ctx, 8, 3.04)
+    st = attn.attn_state_create(ctx, model, 32, raw_tree_tensors(tree.shape, 0))
+    attn.attn_de_place(st, 16)
+    attn.attn_map_hamiltonian(st)
+    attn.attn_ttn_sweep(st)
+    node = tree.top_nodes()[0]
+    attn.attn_move_centre(st, node)
+    H = attn.attn_heff_build(st, node)
+    x0 = attn.attn_node_get(st, node)
+    cfg = attn.attn_get_config(ctx)
+    cfg.lanczos_depth, cfg.lanczos_tol, cfg.matvec_dtype = 60, 1e-14, attn.ATTN_F64
+    attn.attn_set_config(ctx, cfg)
+    th64, _ = attn.attn_eigsolve(H, dev(x0))
+    cfg.lanczos_depth, cfg.lanczos_tol, cfg.matvec_dtype = 20, 1e-13, attn.ATTN_BF16
+    cfg.lanczos_basis = basis
+    cfg.refine_steps = 0
+    attn.attn_set_config(ctx, cfg)
+    th_lo, _ = attn.attn_eigsolve(H, dev(x0))
+    assert abs(th_lo - th64) < 2e-2 * abs(th64)
+    cfg.refine_steps, cfg.refine_tol, cfg.refine_inner = 5, 1e-13, 16
+    attn.attn_set_config(ctx, cfg)
+    t = dev(x0)
+    th, _ = attn.attn_eigsolve(H, t)
+    w = torch.empty_like(t)
+    attn.attn_heff_apply(H, t, w, attn.ATTN_F64)
+    rq = float(torch.dot(t.reshape(-1), w.reshape(-1)) / torch.dot(t.reshape(-1), t.reshape(-1)))
+    assert abs(th - rq) < 1e-12 * abs(rq)
+    assert th >= th64 - 1e-11 * abs(th64) and th - th64 < 1e-11 * abs(th64), (th, th64)
+    attn.attn_heff_destroy(H)
+    attn.attn_state_destroy(st)
+    attn.attn_model_destroy(model)
+    attn.attn_destroy(ctx)
