@@ -638,12 +638,13 @@ def run_sttn(args):
     stream = torch.cuda.current_stream().cuda_stream
     rows = []
     for s_ttn in [int(v) for v in args.sttn_values.split(",")]:
+        # s_ttn = -1: the plain TTN at the same bond dimension (no disentanglers)
         cfg = arm_config(attn, args.sttn_arm)
-        cfg.s_ttn = s_ttn
+        cfg.s_ttn = max(s_ttn, 0)
         ctx = attn.attn_create(cfg, stream)
         model = attn.attn_model_tfim(ctx, Ls, H_FIELD)
         st = attn.attn_state_create(ctx, model, ms, raw)
-        n_de = attn.attn_de_place(st, n // 4)
+        n_de = attn.attn_de_place(st, n // 4 if s_ttn >= 0 else 0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         es = [attn.attn_sweep(st) / n for _ in range(args.max_sweeps)]
@@ -902,7 +903,8 @@ def main():
                     help="converge mode: comma-separated precision arms (f64 first)")
     ap.add_argument("--sweep-arms", default="f64,mixed,mixed_k3",
                     help="sweep mode: comma-separated precision arms (f64 first)")
-    ap.add_argument("--sttn-values", default="0,1,2,3,5", help="sttn mode: S_TTN values to compare")
+    ap.add_argument("--sttn-values", default="-1,0,1,2,3,5",
+                    help="sttn mode: S_TTN values to compare (-1: plain TTN, no disentanglers)")
     ap.add_argument("--sttn-arm", default="mixed_split", help="sttn mode: precision arm of every run")
     ap.add_argument("--phases", action="store_true",
                     help="sweep/converge modes: report stream time per kernel class and local-step phase "
