@@ -107,3 +107,23 @@ def test_unconverged_eigensolve_can_be_reported():
     assert th2 >= th - 1e-12 * abs(th)
     attn.attn_heff_destroy(H)
     attn.attn_destroy(ctx)
+
+
+def test_config_fields_are_validated():
+    """attn_set_config refuses out-of-range choices with ATTN_EINVAL and keeps the old
+    configuration; valid values are accepted."""
+    EINVAL = 1
+    attn, ctx = lib_and_ctx()
+    good = attn.attn_get_config(ctx)
+    for field, bad in (("tc_schedule", 3), ("tc_schedule", -1), ("lanczos_basis", 2), ("de_method", 2),
+                       ("wait_limit_log2", 63), ("lanczos_depth", 61)):
+        cfg = attn.attn_get_config(ctx)
+        setattr(cfg, field, bad)
+        assert _status(attn.attn_set_config, ctx, cfg) == EINVAL, field
+        assert getattr(attn.attn_get_config(ctx), field) == getattr(good, field), field
+    for field, ok in (("tc_schedule", 2), ("lanczos_basis", 1)):
+        cfg = attn.attn_get_config(ctx)
+        setattr(cfg, field, ok)
+        attn.attn_set_config(ctx, cfg)
+        assert getattr(attn.attn_get_config(ctx), field) == ok
+    attn.attn_destroy(ctx)
