@@ -43,12 +43,15 @@ def test_de_update_matches_oracle(L, m, n_de, model):
     for k, p in enumerate(probs):
         u_ref, hist = optimise_de(p, np.eye(4))
         u = attn.attn_de_get(st, k)
-        assert abs(en[k, 0] - hist[0]) < 1e-10 * max(1, abs(hist[0])), k
-        assert abs(en[k, 1] - hist[-1]) < 1e-9 * max(1, abs(hist[-1])), k
-        assert np.abs(u - u_ref).max() < 1e-7, k
+        # FP64 on both sides: E_k to 1e-12; u, the result of 15-21 SVD-based iterations,
+        # to 1e-11 (each SVD step may amplify last-bit differences of Gamma_k by the inverse
+        # gap of its singular values; on these cases the deviation measured 1e-15..1e-13)
+        assert abs(en[k, 0] - hist[0]) < 1e-12 * max(1, abs(hist[0])), k
+        assert abs(en[k, 1] - hist[-1]) < 1e-12 * max(1, abs(hist[-1])), k
+        assert np.abs(u - u_ref).max() < 1e-11, k
         assert np.abs(u.T @ u - np.eye(4)).max() < 1e-12
         dref += hist[-1] - hist[0]
-    assert abs(dE - dref) < 1e-8 * max(1.0, abs(dref))
+    assert abs(dE - dref) < 1e-12 * max(1.0, abs(dref))
     attn.attn_state_destroy(st)
     attn.attn_model_destroy(mod)
     attn.attn_destroy(ctx)
